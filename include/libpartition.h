@@ -1,0 +1,166 @@
+/*
+ * libpartition -- in-place parallel partition on one GB300 GPU (sm_103a).
+ *
+ * Implements the algorithms of Kuszmaul & Westover, "In-Place
+ * Parallel-Partition Algorithms using Exclusive-Read-and-Write Memory"
+ * (arXiv 2004.12532): the Smoothed Striding Algorithm (Sec. 4), the Strided
+ * Algorithm it builds on (Sec. 4, after Francis & Pannan), the
+ * Blocked-Prefix-Sum ("low-space") partition (Sec. 3), and a quicksort built on
+ * the partition (Sec. 5, "A Full Quicksort").
+ *
+ * The problem (Sec. 2, "The Parallel Partition Problem"): reorder an array so
+ * that every predecessor precedes every successor.  Here the decider is
+ * dec(x) = [x <= pivot]: keys <= pivot are predecessors.  Arrays are
+ * 0-indexed; every partition reports the split t = number of predecessors, so
+ * keys[0..t) <= pivot < keys[t..n) afterwards, and the array is a permutation
+ * of its input.  The order inside each side is unspecified but deterministic
+ * for a given input, seed and device.
+ *
+ * Conventions for every call:
+ *   - key / value pointers are DEVICE pointers owned by the caller; the library
+ *     reorders them in place and never frees or reallocates them.  They must be
+ *     naturally aligned (8 bytes for uint64_t, 4 for uint32_t); 16-byte
+ *     alignment is not required.
+ *   - work is enqueued on the caller's cudaStream_t and is stream-ordered.
+ *     Calls that take a host `*_out` pointer synchronise that stream before
+ *     returning; `_async` calls do not.
+ *   - scratch memory belongs to the lp_ctx (allocated once at creation, a few
+ *     KB plus what a call needs, never more than 1% of the array's bytes for
+ *     the partition calls); lp_ctx_aux_bytes reports it.  Calls that share an
+ *     lp_ctx share its scratch: issue them on one stream, or synchronise
+ *     between them.
+ *   - every call returns an lp_status and never aborts the process; on error
+ *     lp_ctx_last_error() describes it.  On LP_ERR_TIMEOUT or LP_ERR_INTERNAL
+ *     the array is a permutation of its input but may not be partitioned.
+ *   - n == 0 is valid and returns t = 0; a null key pointer with n > 0 is
+ *     LP_ERR_INVALID_ARG.
+ */
+#ifndef LIBPARTITION_H
+#define LIBPARTITION_H
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LP_OK = 0,
+  LP_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad variant, ... */
+  LP_ERR_MISALIGNED = 2,  /* only from calls that require 16-byte aligned input */
+  LP_ERR_OOM = 3,         /* a scratch allocation failed */
+  LP_ERR_BUDGET = 4,      /* the server's memory budget cannot hold a request */
+  LP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  LP_ERR_CUDA = 6,        /* a CUDA runtime call failed; see lp_ctx_last_error */
+  LP_ERR_INTERNAL = 7     /* a device-side consistency check failed */
+} lp_status;
+
+typedef enum {
+  LP_SMOOTHED = 0, /* Recursive Smoothed Striding (Sec. 4) */
+  LP_STRIDED = 1,  /* Strided Algorithm: the step with X == 0, then cleanup */
+  LP_LOWSPACE = 2, /* Blocked-Prefix-Sum partition (Sec. 3), explicit prefix */
+  LP_HYBRID = 3    /* Hybrid Smoothed Striding: one step, residual by LOWSPACE */
+} lp_variant;
+
+typedef struct lp_ctx lp_ctx;
+
+/* Creates a context on CUDA device `device` (which becomes current for the
+ * calling thread).  Queries the SM count and allocates the fixed scratch. */
+lp_status lp_ctx_create(lp_ctx **ctx, int device);
+/* Frees the context's scratch.  Outstanding work must have completed. */
+lp_status lp_ctx_destroy(lp_ctx *ctx);
+/* Message of the last error on this context ("" when none).  Owned by ctx. */
+const char *lp_ctx_last_error(const lp_ctx *ctx);
+/* Device scratch bytes held by the context (fixed part + the largest
+ * per-call part so far). */
+uint64_t lp_ctx_aux_bytes(const lp_ctx *ctx);
+/* Kernel launches made by the last call on this context. */
+uint64_t lp_ctx_last_launches(const lp_ctx *ctx);
+/* Number of CTAs the streaming kernels use per launch on this device. */
+uint32_t lp_ctx_grid(const lp_ctx *ctx);
+
+/* Partial steps a Smoothed / Strided partition may run (the last one is a
+ * single-group finish, the paper's base case). */
+#define LP_MAX_LEVELS 8
+/* enable != 0: later partition calls on ctx record a CUDA event on their
+ * stream before each partial-step kernel and after the last one. */
+lp_status lp_ctx_set_timing(lp_ctx *ctx, int enable);
+/* Level structure of the last Smoothed / Strided partition call on ctx (the
+ * recursion of Sec. 4 on [v_min, v_max)): for level L < LP_MAX_LEVELS,
+ * ranges[4L..4L+3] = {lo, hi, b, g} of the range that level partitioned
+ * (all zero for a level that had nothing left to do), and, when timing was
+ * enabled for that call, ms[L] = the level kernel's duration in milliseconds
+ * (ms may be NULL).  Synchronises the last call's stream.  *levels receives
+ * LP_MAX_LEVELS. */
+lp_status lp_ctx_level_stats(lp_ctx *ctx, uint64_t *ranges, float *ms, int *levels);
+
+/* ---------------------------------------------------------------- partition
+ * Partition keys[0..n) by [x <= pivot] (Sec. 2).  `variant` selects the
+ * algorithm; `seed` drives the random offsets X of Smoothed Striding (Sec. 4,
+ * "Set each of X[1..s] to be uniformly random") and is ignored by variants
+ * without randomness.  *split_out (host) receives t; the call synchronises
+ * `stream`.  */
+lp_status lp_partition_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
+                           lp_variant variant, uint64_t seed, cudaStream_t stream,
+                           uint64_t *split_out);
+lp_status lp_partition_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t pivot,
+                           lp_variant variant, uint64_t seed, cudaStream_t stream,
+                           uint64_t *split_out);
+/* Key + payload: vals[i] moves with keys[i].  Two separate arrays of n
+ * entries (structure of arrays). */
+lp_status lp_partition_kv_u64(lp_ctx *ctx, uint64_t *keys, uint64_t *vals, uint64_t n,
+                              uint64_t pivot, lp_variant variant, uint64_t seed,
+                              cudaStream_t stream, uint64_t *split_out);
+/* As above without synchronising: t is written to the device word *d_split
+ * when the stream reaches the end of the call. */
+lp_status lp_partition_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
+                                 lp_variant variant, uint64_t seed, cudaStream_t stream,
+                                 uint64_t *d_split);
+lp_status lp_partition_u32_async(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t pivot,
+                                 lp_variant variant, uint64_t seed, cudaStream_t stream,
+                                 uint64_t *d_split);
+lp_status lp_partition_kv_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t *vals,
+                                    uint64_t n, uint64_t pivot, lp_variant variant,
+                                    uint64_t seed, cudaStream_t stream, uint64_t *d_split);
+
+/* ------------------------------------------------- one Partial Partition Step
+ * Runs exactly one Partial Partition Step (Sec. 4, "Formal Algorithm
+ * Description"; Proposition 4.2) on keys[0..n) with explicit parameters:
+ * lines of b keys, g groups, chunk j's offset X[j] = floor(r_j * g / 2^64)
+ * where r_j is output j of SplitMix64 started at sigma, and sigma is output
+ * `level` of SplitMix64 started at `seed` (strided != 0 forces X == 0).
+ * Group i holds line j*g + (X[j]+i) mod g of every chunk j; lines past the end
+ * are virtual.  Each group ends predecessors-first in its own slot order.
+ * Results (host): *vmin / *vmax = min / max over non-empty groups of v_i, the
+ * position of group i's first successor slot (one past its last slot when it
+ * has none); *count = number of predecessors.  Afterwards keys[p] <= pivot
+ * for p < vmin and keys[p] > pivot for p >= vmax.
+ * Requires keys 16-byte aligned, n * sizeof(key) and b * sizeof(key)
+ * multiples of 16, b * sizeof(key) <= 4096 (2048 for kv), g >= 1; otherwise
+ * LP_ERR_MISALIGNED / LP_ERR_INVALID_ARG.  Synchronises `stream`. */
+lp_status lp_smoothed_step_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
+                               uint64_t b, uint64_t g, uint64_t seed, uint64_t level,
+                               int strided, cudaStream_t stream, uint64_t *vmin,
+                               uint64_t *vmax, uint64_t *count);
+lp_status lp_smoothed_step_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t pivot,
+                               uint64_t b, uint64_t g, uint64_t seed, uint64_t level,
+                               int strided, cudaStream_t stream, uint64_t *vmin,
+                               uint64_t *vmax, uint64_t *count);
+
+/* ------------------------------------------------------- synthetic inputs
+ * Fill d_keys[0..n) with outputs 0..n-1 of SplitMix64 started at `seed`
+ * (Steele, Lea, Flood 2014); the u32 form keeps the low 32 bits.  These are
+ * the seeded uniform inputs of the benchmark workloads, not part of the
+ * partition. */
+lp_status lp_fill_uniform_u64(uint64_t *d_keys, uint64_t n, uint64_t seed,
+                              cudaStream_t stream);
+lp_status lp_fill_uniform_u32(uint32_t *d_keys, uint64_t n, uint64_t seed,
+                              cudaStream_t stream);
+/* d_vals[i] = i. */
+lp_status lp_fill_iota_u64(uint64_t *d_vals, uint64_t n, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBPARTITION_H */

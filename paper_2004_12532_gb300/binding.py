@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libpartition's C ABI (include/libpartition.h).
+
+Argument marshalling only: every function here forwards to the function of
+the same name in libpartition.so, passing a torch CUDA tensor's device pointer,
+its element count and the current CUDA stream.  No computation happens here,
+and there is no CPU fallback: if the library is missing, the first call raises.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpartition.so")
+
+LP_OK = 0
+LP_ERR_INVALID_ARG = 1
+LP_ERR_MISALIGNED = 2
+LP_ERR_OOM = 3
+LP_ERR_BUDGET = 4
+LP_ERR_TIMEOUT = 5
+LP_ERR_CUDA = 6
+LP_ERR_INTERNAL = 7
+
+LP_SMOOTHED = 0
+LP_STRIDED = 1
+LP_LOWSPACE = 2
+LP_HYBRID = 3
+LP_MAX_LEVELS = 8
+
+_u64 = C.c_uint64
+_u32 = C.c_uint32
+_p = C.c_void_p
+_i = C.c_int
+_pu64 = C.POINTER(C.c_uint64)
+
+_SIGS = {
+    "lp_ctx_create": (_i, [C.POINTER(_p), _i]),
+    "lp_ctx_destroy": (_i, [_p]),
+    "lp_ctx_last_error": (C.c_char_p, [_p]),
+    "lp_ctx_aux_bytes": (_u64, [_p]),
+    "lp_ctx_last_launches": (_u64, [_p]),
+    "lp_ctx_grid": (_u32, [_p]),
+    "lp_ctx_set_timing": (_i, [_p, _i]),
+    "lp_ctx_level_stats": (_i, [_p, _pu64, C.POINTER(C.c_float), C.POINTER(_i)]),
+    "lp_partition_u64": (_i, [_p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
+    "lp_partition_u32": (_i, [_p, _p, _u64, _u32, _i, _u64, _p, _pu64]),
+    "lp_partition_kv_u64": (_i, [_p, _p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
+    "lp_partition_u64_async": (_i, [_p, _p, _u64, _u64, _i, _u64, _p, _p]),
+    "lp_partition_u32_async": (_i, [_p, _p, _u64, _u32, _i, _u64, _p, _p]),
+    "lp_partition_kv_u64_async": (_i, [_p, _p, _p, _u64, _u64, _i, _u64, _p, _p]),
+    "lp_smoothed_step_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _u64, _u64, _i, _p,
+                                  _pu64, _pu64, _pu64]),
+    "lp_smoothed_step_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _u64, _u64, _i, _p,
+                                  _pu64, _pu64, _pu64]),
+    "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
+    "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
+    "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libpartition.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libpartition.so is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class LPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libpartition status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, bits):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.element_size() * 8 != bits:
+        raise TypeError("expected %d-bit elements, got %s" % (bits, t.dtype))
+    if not t.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr()), t.numel()
+
+
+class Ctx:
+    """An lp_ctx on one CUDA device (lp_ctx_create / lp_ctx_destroy)."""
+
+    def __init__(self, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = C.c_void_p()
+        st = lib().lp_ctx_create(C.byref(h), self.device)
+        if st != LP_OK:
+            raise LPError(st, "lp_ctx_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st):
+        if st != LP_OK:
+            raise LPError(st, lib().lp_ctx_last_error(self.h).decode())
+        return st
+
+    @property
+    def aux_bytes(self):
+        return int(lib().lp_ctx_aux_bytes(self.h))
+
+    @property
+    def last_launches(self):
+        return int(lib().lp_ctx_last_launches(self.h))
+
+    @property
+    def grid(self):
+        return int(lib().lp_ctx_grid(self.h))
+
+    def set_timing(self, on=True):
+        self.check(lib().lp_ctx_set_timing(self.h, 1 if on else 0))
+
+    def level_stats(self):
+        """[(lo, hi, b, g, ms)] for each level of the last partition call."""
+        rng = (C.c_uint64 * (4 * LP_MAX_LEVELS))()
+        ms = (C.c_float * LP_MAX_LEVELS)()
+        nl = C.c_int()
+        self.check(lib().lp_ctx_level_stats(self.h, rng, ms, C.byref(nl)))
+        return [(int(rng[4 * i]), int(rng[4 * i + 1]), int(rng[4 * i + 2]), int(rng[4 * i + 3]),
+                 float(ms[i])) for i in range(nl.value)]
+
+
+def lp_ctx_create(device=None):
+    return Ctx(device)
+
+
+def lp_partition_u64(ctx, keys, pivot, variant=LP_SMOOTHED, seed=0, stream=None):
+    p, n = _dev_ptr(keys, 64)
+    t = C.c_uint64()
+    ctx.check(lib().lp_partition_u64(ctx.h, p, n, int(pivot), int(variant), int(seed),
+                                     _stream(stream), C.byref(t)))
+    return int(t.value)
+
+
+def lp_partition_u32(ctx, keys, pivot, variant=LP_SMOOTHED, seed=0, stream=None):
+    p, n = _dev_ptr(keys, 32)
+    t = C.c_uint64()
+    ctx.check(lib().lp_partition_u32(ctx.h, p, n, int(pivot), int(variant), int(seed),
+                                     _stream(stream), C.byref(t)))
+    return int(t.value)
+
+
+def lp_partition_kv_u64(ctx, keys, vals, pivot, variant=LP_SMOOTHED, seed=0, stream=None):
+    p, n = _dev_ptr(keys, 64)
+    q, m = _dev_ptr(vals, 64)
+    if m != n:
+        raise ValueError("keys and vals differ in length")
+    t = C.c_uint64()
+    ctx.check(lib().lp_partition_kv_u64(ctx.h, p, q, n, int(pivot), int(variant), int(seed),
+                                        _stream(stream), C.byref(t)))
+    return int(t.value)
+
+
+def lp_partition_u64_async(ctx, keys, pivot, d_split, variant=LP_SMOOTHED, seed=0, stream=None):
+    p, n = _dev_ptr(keys, 64)
+    s, _ = _dev_ptr(d_split, 64)
+    return ctx.check(lib().lp_partition_u64_async(ctx.h, p, n, int(pivot), int(variant),
+                                                  int(seed), _stream(stream), s))
+
+
+def lp_partition_u32_async(ctx, keys, pivot, d_split, variant=LP_SMOOTHED, seed=0, stream=None):
+    p, n = _dev_ptr(keys, 32)
+    s, _ = _dev_ptr(d_split, 64)
+    return ctx.check(lib().lp_partition_u32_async(ctx.h, p, n, int(pivot), int(variant),
+                                                  int(seed), _stream(stream), s))
+
+
+def lp_partition_kv_u64_async(ctx, keys, vals, pivot, d_split, variant=LP_SMOOTHED, seed=0,
+                              stream=None):
+    p, n = _dev_ptr(keys, 64)
+    q, _ = _dev_ptr(vals, 64)
+    s, _ = _dev_ptr(d_split, 64)
+    return ctx.check(lib().lp_partition_kv_u64_async(ctx.h, p, q, n, int(pivot), int(variant),
+                                                     int(seed), _stream(stream), s))
+
+
+def lp_smoothed_step(ctx, keys, pivot, b, g, seed=0, level=0, strided=False, stream=None):
+    """One Partial Partition Step; returns (vmin, vmax, count)."""
+    bits = keys.element_size() * 8
+    p, n = _dev_ptr(keys, bits)
+    f = lib().lp_smoothed_step_u64 if bits == 64 else lib().lp_smoothed_step_u32
+    vmin, vmax, cnt = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    ctx.check(f(ctx.h, p, n, int(pivot), int(b), int(g), int(seed), int(level),
+                1 if strided else 0, _stream(stream), C.byref(vmin), C.byref(vmax),
+                C.byref(cnt)))
+    return int(vmin.value), int(vmax.value), int(cnt.value)
+
+
+def lp_fill_uniform_u64(keys, seed, stream=None):
+    p, n = _dev_ptr(keys, 64)
+    st = lib().lp_fill_uniform_u64(p, n, int(seed), _stream(stream))
+    if st != LP_OK:
+        raise LPError(st, "lp_fill_uniform_u64")
+
+
+def lp_fill_uniform_u32(keys, seed, stream=None):
+    p, n = _dev_ptr(keys, 32)
+    st = lib().lp_fill_uniform_u32(p, n, int(seed), _stream(stream))
+    if st != LP_OK:
+        raise LPError(st, "lp_fill_uniform_u32")
+
+
+def lp_fill_iota_u64(vals, stream=None):
+    p, n = _dev_ptr(vals, 64)
+    st = lib().lp_fill_iota_u64(p, n, _stream(stream))
+    if st != LP_OK:
+        raise LPError(st, "lp_fill_iota_u64")

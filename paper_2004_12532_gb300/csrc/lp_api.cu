@@ -1,0 +1,325 @@
+// lp_api.cu -- the C ABI of libpartition (include/libpartition.h): argument
+// checks, context and scratch ownership, status mapping.  Every compute step
+// runs in the kernels of lp_kernels.cu and its siblings.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/libpartition.h"
+#include "lp_device.cuh"
+#include "lp_launch.h"
+
+struct lp_ctx {
+  int device = 0;
+  uint32_t grid_u64 = 0, grid_u32 = 0, grid_kv = 0;
+  void* d_scratch = nullptr;      // fixed scratch: descriptors, status, split
+  size_t scratch_bytes = 0;
+  uint64_t* h_pinned = nullptr;   // 64 bytes of pinned host memory for read-back
+  uint64_t aux_bytes = 0;
+  uint64_t last_launches = 0;
+  std::string err;
+  lp::TaskScratch task{};
+  bool timing = false;
+  bool events_made = false;
+  bool last_timed = false;
+  cudaEvent_t ev[lp::kMaxLevels + 1];
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+lp_status fail(lp_ctx* c, lp_status s, const char* what) {
+  if (c) c->err = what;
+  return s;
+}
+
+lp_status cuda_fail(lp_ctx* c, cudaError_t e, const char* where) {
+  if (c) {
+    c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return LP_ERR_CUDA;
+}
+
+lp_status status_to_lp(lp_ctx* c, uint32_t st) {
+  if (st == 0) return LP_OK;
+  if (st & lp::kStatTimeout) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  return fail(c, LP_ERR_INTERNAL, "device consistency check failed");
+}
+
+template <typename T>
+bool aligned_to(const T* p, uintptr_t a) {
+  return (reinterpret_cast<uintptr_t>(p) % a) == 0;
+}
+
+// Synchronous tail shared by the sync partition calls: read back split and
+// status words.
+lp_status read_back(lp_ctx* c, cudaStream_t stream, uint64_t* split_out) {
+  cudaError_t e = cudaMemcpyAsync(c->h_pinned, c->task.split, 8, cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read split");
+  e = cudaMemcpyAsync(c->h_pinned + 1, c->task.status, 4, cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+  e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  uint32_t st = (uint32_t)(c->h_pinned[1] & 0xffffffffu);
+  if (split_out) *split_out = c->h_pinned[0];
+  return status_to_lp(c, st);
+}
+
+template <typename T, bool KV>
+lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot,
+                         lp_variant variant, uint64_t seed, cudaStream_t stream,
+                         uint64_t* split_out, uint64_t* d_split) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->err.clear();
+  c->last_launches = 0;
+  if (variant != LP_SMOOTHED && variant != LP_STRIDED)
+    return fail(c, LP_ERR_INVALID_ARG, "variant not available");
+  if (n > 0 && (!keys || (KV && !vals))) return fail(c, LP_ERR_INVALID_ARG, "null array");
+  if (!aligned_to(keys, sizeof(T)) || (KV && !aligned_to(vals, 8)))
+    return fail(c, LP_ERR_INVALID_ARG, "array not naturally aligned");
+  if (KV && n > lp::small_limit(sizeof(T), true) &&
+      (reinterpret_cast<uintptr_t>(keys) & 15) != (reinterpret_cast<uintptr_t>(vals) & 15))
+    return fail(c, LP_ERR_MISALIGNED, "keys and vals must share their offset mod 16");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  lp::TaskScratch S = c->task;
+  if (d_split) S.split = d_split;
+  if (n == 0) {
+    if (d_split) {
+      e = cudaMemsetAsync(d_split, 0, 8, stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "memset split");
+    }
+    if (split_out) *split_out = 0;
+    return LP_OK;
+  }
+  lp::LaunchCfg cfg{KV ? c->grid_kv : (sizeof(T) == 8 ? c->grid_u64 : c->grid_u32), stream, 0,
+                    c->timing ? c->ev : nullptr};
+  c->last_timed = c->timing;
+  c->last_stream = stream;
+  e = lp::launch_smoothed<T, KV>(keys, vals, n, pivot, seed, variant == LP_STRIDED ? 1 : 0, S,
+                                 cfg);
+  c->last_launches = cfg.launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "launch");
+  if (split_out) {
+    if (d_split) {
+      e = cudaMemcpyAsync(c->h_pinned, d_split, 8, cudaMemcpyDeviceToHost, stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "read split");
+      e = cudaMemcpyAsync(c->h_pinned + 1, c->task.status, 4, cudaMemcpyDeviceToHost, stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+      e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+      *split_out = c->h_pinned[0];
+      return status_to_lp(c, (uint32_t)c->h_pinned[1]);
+    }
+    return read_back(c, stream, split_out);
+  }
+  return LP_OK;
+}
+
+template <typename T>
+lp_status step_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t b, uint64_t g,
+                    uint64_t seed, uint64_t level, int strided, cudaStream_t stream,
+                    uint64_t* vmin, uint64_t* vmax, uint64_t* count) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->err.clear();
+  c->last_launches = 0;
+  if (!vmin || !vmax || !count) return fail(c, LP_ERR_INVALID_ARG, "null result pointer");
+  if (n > 0 && !keys) return fail(c, LP_ERR_INVALID_ARG, "null array");
+  if (b == 0 || g == 0) return fail(c, LP_ERR_INVALID_ARG, "b and g must be positive");
+  if ((b * sizeof(T)) % 16 != 0 || b * sizeof(T) > 4096)
+    return fail(c, LP_ERR_INVALID_ARG, "b*sizeof(key) must be a multiple of 16, at most 4096");
+  if (!aligned_to(keys, 16) || (n * sizeof(T)) % 16 != 0)
+    return fail(c, LP_ERR_MISALIGNED, "keys must be 16-byte aligned, n*sizeof(key) % 16 == 0");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  if (n == 0) {
+    *vmin = *vmax = *count = 0;
+    return LP_OK;
+  }
+  lp::LaunchCfg cfg{sizeof(T) == 8 ? c->grid_u64 : c->grid_u32, stream, 0, nullptr};
+  c->last_timed = false;
+  c->last_stream = stream;
+  e = lp::launch_step<T>(keys, n, pivot, b, g, seed, level, strided, c->task, cfg);
+  c->last_launches = cfg.launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "launch");
+  // descriptor 0: vmin, vmax, count are its first three words
+  e = cudaMemcpyAsync(c->h_pinned, c->task.desc, 24, cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read result");
+  e = cudaMemcpyAsync(c->h_pinned + 3, c->task.status, 4, cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+  e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  uint64_t lo = c->h_pinned[0], hi = c->h_pinned[1];
+  if (lo == ~0ull) lo = hi = 0;  // every group empty
+  *vmin = lo;
+  *vmax = hi;
+  *count = c->h_pinned[2];
+  return status_to_lp(c, (uint32_t)c->h_pinned[3]);
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_ctx_create(lp_ctx** out, int device) {
+  if (!out) return LP_ERR_INVALID_ARG;
+  *out = nullptr;
+  lp_ctx* c = new (std::nothrow) lp_ctx();
+  if (!c) return LP_ERR_OOM;
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { delete c; return LP_ERR_CUDA; }
+  if ((e = lp::streaming_grid<uint64_t, false>(device, &c->grid_u64)) != cudaSuccess ||
+      (e = lp::streaming_grid<uint32_t, false>(device, &c->grid_u32)) != cudaSuccess ||
+      (e = lp::streaming_grid<uint64_t, true>(device, &c->grid_kv)) != cudaSuccess) {
+    delete c;
+    return LP_ERR_CUDA;
+  }
+  const size_t desc_bytes = lp::level_desc_bytes() * lp::kMaxLevels;
+  c->scratch_bytes = desc_bytes + 256;
+  e = cudaMalloc(&c->d_scratch, c->scratch_bytes);
+  if (e != cudaSuccess) { delete c; return LP_ERR_OOM; }
+  e = cudaMallocHost(reinterpret_cast<void**>(&c->h_pinned), 64);
+  if (e != cudaSuccess) { cudaFree(c->d_scratch); delete c; return LP_ERR_OOM; }
+  unsigned char* base = static_cast<unsigned char*>(c->d_scratch);
+  c->task.desc = reinterpret_cast<lp::LevelDesc*>(base);
+  c->task.status = reinterpret_cast<uint32_t*>(base + desc_bytes);
+  c->task.split = reinterpret_cast<uint64_t*>(base + desc_bytes + 64);
+  c->aux_bytes = c->scratch_bytes;
+  *out = c;
+  return LP_OK;
+}
+
+lp_status lp_ctx_destroy(lp_ctx* c) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (c->events_made)
+    for (int i = 0; i <= lp::kMaxLevels; i++) cudaEventDestroy(c->ev[i]);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+  return LP_OK;
+}
+
+const char* lp_ctx_last_error(const lp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+uint64_t lp_ctx_aux_bytes(const lp_ctx* c) { return c ? c->aux_bytes : 0; }
+uint64_t lp_ctx_last_launches(const lp_ctx* c) { return c ? c->last_launches : 0; }
+uint32_t lp_ctx_grid(const lp_ctx* c) { return c ? c->grid_u64 : 0; }
+
+lp_status lp_ctx_set_timing(lp_ctx* c, int enable) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  if (enable && !c->events_made) {
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    for (int i = 0; i <= lp::kMaxLevels; i++) {
+      e = cudaEventCreate(&c->ev[i]);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    }
+    c->events_made = true;
+  }
+  c->timing = enable != 0;
+  return LP_OK;
+}
+
+lp_status lp_ctx_level_stats(lp_ctx* c, uint64_t* ranges, float* ms, int* levels) {
+  if (!c || !ranges || !levels) return LP_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  const size_t db = lp::level_desc_bytes();
+  for (int L = 0; L < lp::kMaxLevels; L++) {
+    uint64_t w[8];
+    e = cudaMemcpy(w, reinterpret_cast<unsigned char*>(c->task.desc) + L * db, sizeof(w),
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read level");
+    ranges[4 * L + 0] = w[3];  // lo
+    ranges[4 * L + 1] = w[4];  // hi
+    ranges[4 * L + 2] = w[5];  // b
+    ranges[4 * L + 3] = w[6];  // g
+    if (ms) {
+      ms[L] = 0.f;
+      if (c->last_timed) {
+        e = cudaEventElapsedTime(&ms[L], c->ev[L], c->ev[L + 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "event elapsed");
+      }
+    }
+  }
+  *levels = lp::kMaxLevels;
+  return LP_OK;
+}
+
+lp_status lp_partition_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
+                           lp_variant v, uint64_t seed, cudaStream_t s, uint64_t* split_out) {
+  if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
+  return partition_impl<uint64_t, false>(c, keys, nullptr, n, pivot, v, seed, s, split_out,
+                                         nullptr);
+}
+lp_status lp_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
+                           lp_variant v, uint64_t seed, cudaStream_t s, uint64_t* split_out) {
+  if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
+  return partition_impl<uint32_t, false>(c, keys, nullptr, n, pivot, v, seed, s, split_out,
+                                         nullptr);
+}
+lp_status lp_partition_kv_u64(lp_ctx* c, uint64_t* keys, uint64_t* vals, uint64_t n,
+                              uint64_t pivot, lp_variant v, uint64_t seed, cudaStream_t s,
+                              uint64_t* split_out) {
+  if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
+  return partition_impl<uint64_t, true>(c, keys, vals, n, pivot, v, seed, s, split_out,
+                                        nullptr);
+}
+lp_status lp_partition_u64_async(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
+                                 lp_variant v, uint64_t seed, cudaStream_t s,
+                                 uint64_t* d_split) {
+  if (!d_split) return fail(c, LP_ERR_INVALID_ARG, "null d_split");
+  return partition_impl<uint64_t, false>(c, keys, nullptr, n, pivot, v, seed, s, nullptr,
+                                         d_split);
+}
+lp_status lp_partition_u32_async(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
+                                 lp_variant v, uint64_t seed, cudaStream_t s,
+                                 uint64_t* d_split) {
+  if (!d_split) return fail(c, LP_ERR_INVALID_ARG, "null d_split");
+  return partition_impl<uint32_t, false>(c, keys, nullptr, n, pivot, v, seed, s, nullptr,
+                                         d_split);
+}
+lp_status lp_partition_kv_u64_async(lp_ctx* c, uint64_t* keys, uint64_t* vals, uint64_t n,
+                                    uint64_t pivot, lp_variant v, uint64_t seed,
+                                    cudaStream_t s, uint64_t* d_split) {
+  if (!d_split) return fail(c, LP_ERR_INVALID_ARG, "null d_split");
+  return partition_impl<uint64_t, true>(c, keys, vals, n, pivot, v, seed, s, nullptr, d_split);
+}
+
+lp_status lp_smoothed_step_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
+                               uint64_t b, uint64_t g, uint64_t seed, uint64_t level,
+                               int strided, cudaStream_t s, uint64_t* vmin, uint64_t* vmax,
+                               uint64_t* count) {
+  return step_impl<uint64_t>(c, keys, n, pivot, b, g, seed, level, strided, s, vmin, vmax,
+                             count);
+}
+lp_status lp_smoothed_step_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
+                               uint64_t b, uint64_t g, uint64_t seed, uint64_t level,
+                               int strided, cudaStream_t s, uint64_t* vmin, uint64_t* vmax,
+                               uint64_t* count) {
+  return step_impl<uint32_t>(c, keys, n, pivot, b, g, seed, level, strided, s, vmin, vmax,
+                             count);
+}
+
+lp_status lp_fill_uniform_u64(uint64_t* d, uint64_t n, uint64_t seed, cudaStream_t s) {
+  if (n && !d) return LP_ERR_INVALID_ARG;
+  if (!n) return LP_OK;
+  return lp::launch_fill_u64(d, n, seed, s) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+lp_status lp_fill_uniform_u32(uint32_t* d, uint64_t n, uint64_t seed, cudaStream_t s) {
+  if (n && !d) return LP_ERR_INVALID_ARG;
+  if (!n) return LP_OK;
+  return lp::launch_fill_u32(d, n, seed, s) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+lp_status lp_fill_iota_u64(uint64_t* d, uint64_t n, cudaStream_t s) {
+  if (n && !d) return LP_ERR_INVALID_ARG;
+  if (!n) return LP_OK;
+  return lp::launch_iota_u64(d, n, s) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// lp_launch.h -- internal host-side interface between the C ABI (lp_api.cu)
+// and the kernel translation units.  Not part of the public API.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace lp {
+
+struct LevelDesc;
+
+constexpr int kMaxLevels = 8;  // partial steps per partition; the last is a forced finish
+
+// Scratch one partition task needs in device memory.
+struct TaskScratch {
+  LevelDesc* desc;     // kMaxLevels records
+  uint32_t* status;    // device status bits
+  uint64_t* split;     // where the split t is written
+};
+
+struct LaunchCfg {
+  uint32_t grid;       // CTAs of the streaming kernels
+  cudaStream_t stream;
+  uint64_t launches;   // incremented per kernel launch
+  cudaEvent_t* level_events;  // optional, kMaxLevels + 1 events around the levels
+};
+
+// Keys-only (KV = false, vals == nullptr) and key+payload (KV = true, T = uint64_t).
+// Full Recursive Smoothed Striding partition (strided != 0: the first step uses
+// X == 0, i.e. the Strided Algorithm's partial step).
+template <typename T, bool KV>
+cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64_t seed,
+                            int strided, const TaskScratch& S, LaunchCfg& cfg);
+
+// One Partial Partition Step with explicit parameters over keys[0..n).
+template <typename T>
+cudaError_t launch_step(T* keys, uint64_t n, T pivot, uint64_t b, uint64_t g, uint64_t seed,
+                        uint64_t level, int strided, const TaskScratch& S, LaunchCfg& cfg);
+
+// Occupancy-derived grid for the streaming kernels.
+template <typename T, bool KV>
+cudaError_t streaming_grid(int device, uint32_t* grid);
+
+uint64_t small_limit(uint32_t key_bytes, bool kv);
+
+cudaError_t launch_fill_u64(uint64_t* d, uint64_t n, uint64_t seed, cudaStream_t s);
+cudaError_t launch_fill_u32(uint32_t* d, uint64_t n, uint64_t seed, cudaStream_t s);
+cudaError_t launch_iota_u64(uint64_t* d, uint64_t n, cudaStream_t s);
+
+// Size of one LevelDesc (the struct is opaque to lp_api.cu).
+size_t level_desc_bytes();
+
+}  // namespace lp
