@@ -26,7 +26,7 @@ LP_SMOOTHED = 0
 LP_STRIDED = 1
 LP_LOWSPACE = 2
 LP_HYBRID = 3
-LP_MAX_LEVELS = 8
+LP_MAX_LEVELS = 10
 
 _u64 = C.c_uint64
 _u32 = C.c_uint32

@@ -53,58 +53,73 @@ __device__ __forceinline__ bool level_range(const LevelArgs& a, const LevelDesc*
 }
 
 template <typename T, bool KV>
-__global__ void __launch_bounds__(kThreads) level_kernel(T* keys, uint64_t* vals, LevelArgs a,
-                                                         const LevelDesc* in, LevelDesc* out,
-                                                         uint32_t* status) {
+__global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint64_t* vals,
+                                                                   LevelArgs a,
+                                                                   const LevelDesc* in,
+                                                                   LevelDesc* out,
+                                                                   uint32_t* status) {
   using R = Tr<T, KV>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  StreamSmem<T, KV>& sm = *reinterpret_cast<StreamSmem<T, KV>*>(smem_raw);
 
   uint64_t lo, hi;
   if (!level_range(a, in, R::A, lo, hi)) return;
   const uint64_t n = hi - lo;
+  const uint64_t total_warps = (uint64_t)gridDim.x * R::Warps;
 
   uint64_t b, g;
   if (a.fixed_b) {
     b = a.fixed_b;
     g = a.fixed_g;
   } else {
-    StepParams P = choose_params(n, R::K, gridDim.x, R::LineBytes);
+    const StepParams P = choose_params(n, R::K, total_warps, R::LineBytes, R::FinishKeys);
     b = P.b;
     g = P.g;
+    if (a.force_finish && g != 0) g = 1;  // last level: one group takes the rest
   }
-  if (a.force_finish) g = 1;
-  const StepGeom G = make_geom(n, b, g, level_seed(a.seed, a.level), a.strided);
-  if (blockIdx.x >= G.g) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out->lo = lo; out->hi = hi; out->b = b; out->g = g;
+  }
+  if (g == 0) {
+    // the paper's base case: one CTA partitions the range in shared memory
+    if (blockIdx.x != 0) return;
+    const uint32_t cnt = cta_partition_smem<T, KV>(keys + lo, KV ? vals + lo : nullptr,
+                                                   (uint32_t)n, (T)a.pivot, smem_raw);
+    if (threadIdx.x == 0) {
+      out->vmin = lo + cnt;
+      out->vmax = lo + cnt;
+      out->count = cnt;
+    }
+    return;
+  }
 
-  if (threadIdx.x == 0) {
-    for (uint32_t s = 0; s < kStages; s++) mbar_init(&sm.bar[s], 1);
-    sm.abort_flag = 0u;
+  const StepGeom G = make_geom(n, b, g, level_seed(a.seed, a.level), a.strided);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint64_t gw = (uint64_t)blockIdx.x * R::Warps + warp;
+  if (gw >= G.g) return;  // warps are independent: no CTA barrier below
+  WarpSmem<T, KV>& ws = reinterpret_cast<WarpSmem<T, KV>*>(smem_raw)[warp];
+  if (lane == 0) {
+    for (uint32_t s = 0; s < kStages; s++) mbar_init(&ws.bar[s], 1);
     fence_mbar_init();
     fence_proxy_async_smem();
-    if (blockIdx.x == 0) {
-      out->lo = lo; out->hi = hi; out->b = b; out->g = g;
-    }
   }
-  __syncthreads();
+  __syncwarp();
 
   uint32_t phase = 0;
   T* base = keys + lo;
   uint64_t* vbase = KV ? vals + lo : nullptr;
   const T pivot = (T)a.pivot;
-  for (uint64_t i = blockIdx.x; i < G.g; i += gridDim.x) {
+  for (uint64_t i = gw; i < G.g; i += total_warps) {
     const int64_t nl = (int64_t)group_num_lines(G, i);
     uint64_t k = 0;
-    stream_group<T, KV>(base, vbase, G, i, nl, pivot, sm, phase, k, status);
-    if (sm.abort_flag) break;
-    if (nl > 0 && threadIdx.x == 0) {
+    if (!warp_stream_group<T, KV>(base, vbase, G, i, nl, pivot, ws, phase, k, status)) break;
+    if (nl > 0 && lane == 0) {
       const unsigned long long v = lo + group_split_pos(G, i, (uint64_t)nl, k);
       atomicMin(&out->vmin, v);
       atomicMax(&out->vmax, v);
       atomicAdd(&out->count, (unsigned long long)k);
     }
   }
-  if (threadIdx.x == 0) bulk_wait_all<0>();
+  if (lane == 0) bulk_wait_all<0>();
 }
 
 // Head keys [0, h) and tail keys [body_end, n) lie outside the 16-byte aligned
@@ -153,59 +168,23 @@ __global__ void finalize_kernel(T* keys, uint64_t* vals, uint64_t n, uint64_t h,
   *split = t;
 }
 
-// Whole partition of n <= small_limit keys in one CTA: keys staged in shared
-// memory, each thread ranks a contiguous slice, and every key is written once
-// to its final position (predecessors in order, then successors in order).
-constexpr uint32_t kSmallBytes = 64 * 1024;
-
 uint64_t small_limit(uint32_t key_bytes, bool kv) {
-  return kSmallBytes / (key_bytes + (kv ? 8u : 0u));
+  return kFinishBytes / (key_bytes + (kv ? 8u : 0u));
 }
 
+// Whole partition of an array of n <= small_limit keys in one CTA.
 template <typename T, bool KV>
-__global__ void __launch_bounds__(kThreads) small_kernel(T* keys, uint64_t* vals, uint32_t n,
-                                                         T pivot, uint64_t* split) {
+__global__ void __launch_bounds__(Tr<T, KV>::Threads) small_kernel(T* keys, uint64_t* vals,
+                                                                   uint32_t n, T pivot,
+                                                                   uint64_t* split) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* sk = reinterpret_cast<T*>(smem_raw);
-  uint64_t* sv = reinterpret_cast<uint64_t*>(smem_raw + (size_t)n * sizeof(T) + 16);
-  sv = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(sv) + 15) & ~uintptr_t(15));
-  __shared__ uint32_t wsum[kThreads / 32];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  for (uint32_t q = tid; q < n; q += kThreads) {
-    sk[q] = keys[q];
-    if constexpr (KV) sv[q] = vals[q];
-  }
-  __syncthreads();
-  const uint32_t per = (n + kThreads - 1) / kThreads;
-  const uint32_t s0 = min(n, tid * per), s1 = min(n, s0 + per);
-  uint32_t c = 0;
-  for (uint32_t q = s0; q < s1; q++) c += sk[q] <= pivot;
-  uint32_t incl = c;
-  for (uint32_t o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  uint32_t wb = 0, tot = 0;
-  for (uint32_t w = 0; w < kThreads / 32; w++) {
-    wb += w < warp ? wsum[w] : 0u;
-    tot += wsum[w];
-  }
-  uint32_t pp = wb + incl - c;
-  uint32_t sp = tot + (s0 - (wb + incl - c));
-  for (uint32_t q = s0; q < s1; q++) {
-    const T x = sk[q];
-    const uint32_t d = x <= pivot ? pp++ : sp++;
-    keys[d] = x;
-    if constexpr (KV) vals[d] = sv[q];
-  }
-  if (tid == 0) *split = tot;
+  const uint32_t cnt = cta_partition_smem<T, KV>(keys, vals, n, pivot, smem_raw);
+  if (threadIdx.x == 0) *split = cnt;
 }
 
 template <typename T, bool KV>
 static size_t stream_smem_bytes() {
-  return sizeof(StreamSmem<T, KV>);
+  return level_smem_bytes<T, KV>();
 }
 
 template <typename T, bool KV>
@@ -216,12 +195,13 @@ cudaError_t streaming_grid(int device, uint32_t* grid) {
                            (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(small_kernel<T, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kSmallBytes + 64));
+                           (int)smem);
   if (e != cudaSuccess) return e;
   int sms = 0, per = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, level_kernel<T, KV>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, level_kernel<T, KV>,
+                                                    Tr<T, KV>::Threads, smem);
   if (e != cudaSuccess) return e;
   if (per < 1) per = 1;
   *grid = (uint32_t)(sms * per);
@@ -234,10 +214,10 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
   using R = Tr<T, KV>;
   cudaStream_t st = cfg.stream;
   if (n <= small_limit(R::K, KV)) {
-    size_t smem = (size_t)n * R::K + (KV ? (size_t)n * 8 + 32 : 16);
+    const size_t smem = stream_smem_bytes<T, KV>();
     if (cfg.level_events)
       for (int L = 0; L <= kMaxLevels; L++) cudaEventRecord(cfg.level_events[L], st);
-    small_kernel<T, KV><<<1, kThreads, smem, st>>>(keys, vals, (uint32_t)n, pivot, S.split);
+    small_kernel<T, KV><<<1, R::Threads, smem, st>>>(keys, vals, (uint32_t)n, pivot, S.split);
     cfg.launches++;
     desc_init_kernel<<<1, 32, 0, st>>>(S.desc, kMaxLevels, S.status);
     cfg.launches++;
@@ -265,8 +245,8 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
     a.force_finish = (L == kMaxLevels - 1) ? 1 : 0;
     const LevelDesc* in = L ? S.desc + (L - 1) : nullptr;
     if (cfg.level_events) cudaEventRecord(cfg.level_events[L], st);
-    level_kernel<T, KV><<<cfg.grid, kThreads, smem, st>>>(keys, vals, a, in, S.desc + L,
-                                                          S.status);
+    level_kernel<T, KV><<<cfg.grid, R::Threads, smem, st>>>(keys, vals, a, in, S.desc + L,
+                                                            S.status);
     cfg.launches++;
   }
   if (cfg.level_events) cudaEventRecord(cfg.level_events[kMaxLevels], st);
@@ -294,7 +274,7 @@ cudaError_t launch_step(T* keys, uint64_t n, T pivot, uint64_t b, uint64_t g, ui
   a.fixed_g = g;
   a.strided = strided;
   a.force_finish = 0;
-  level_kernel<T, false><<<cfg.grid, kThreads, stream_smem_bytes<T, false>(), st>>>(
+  level_kernel<T, false><<<cfg.grid, Tr<T, false>::Threads, stream_smem_bytes<T, false>(), st>>>(
       keys, nullptr, a, nullptr, S.desc, S.status);
   cfg.launches++;
   return cudaGetLastError();

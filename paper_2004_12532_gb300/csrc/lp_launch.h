@@ -8,7 +8,7 @@ namespace lp {
 
 struct LevelDesc;
 
-constexpr int kMaxLevels = 8;  // partial steps per partition; the last is a forced finish
+constexpr int kMaxLevels = 10;  // partial steps per partition; the last is a forced finish
 
 // Scratch one partition task needs in device memory.
 struct TaskScratch {

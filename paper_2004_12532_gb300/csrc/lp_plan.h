@@ -19,15 +19,20 @@
 namespace lp {
 
 // ---------------------------------------------------------------- constants
-constexpr uint32_t kLineBytesMax = 4096;   // largest line (stage) in bytes
-constexpr uint32_t kLineBytesMin = 512;    // smallest line used by the parameter rule
+// The streaming kernels give one warp one group (the paper's "serial
+// partition of U_i", one processor per group).  Per warp: kQ line loads in
+// flight per side, two rings (P, S) of kRingLines lines, bulk stores allowed
+// to read smem for up to kPendingFlushes write-backs.
+constexpr uint32_t kLineBytesMax = 512;    // largest line (stage) in key bytes
+constexpr uint32_t kLineBytesMin = 128;    // smallest line used by the parameter rule
 constexpr uint32_t kQ = 4;                 // loads in flight per side (front / back)
-constexpr uint32_t kStages = 2 * kQ;       // input stages per CTA
-constexpr uint32_t kRingBytes = 8 * kLineBytesMax;  // each of the two rings
-constexpr uint32_t kPendingFlushes = 4;    // bulk stores allowed to still read smem
-constexpr uint32_t kThreads = 256;         // threads per CTA of the streaming kernels
-constexpr uint32_t kFinishBytes = 128 * 1024;  // ranges up to this size use one group
-constexpr uint32_t kMinChunks = 128;       // s at least this large when g > 1
+constexpr uint32_t kStages = 2 * kQ;       // input stages per warp
+constexpr uint32_t kRingLines = 8;         // ring capacity, in lines of the largest size
+constexpr uint32_t kPendingFlushes = 2;    // bulk stores allowed to still read smem
+constexpr uint32_t kLineTab = 16;          // issued-line table entries per side
+constexpr uint32_t kBatchMax = 1;          // lines consumed per step
+constexpr uint32_t kFinishBytes = 64 * 1024;  // ranges up to this size: one CTA in smem
+constexpr uint32_t kMinChunks = 64;        // s at least this large when g > 1
 
 // ------------------------------------------------------------ random source
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output k of the generator
@@ -117,27 +122,28 @@ LP_HD uint64_t group_split_pos(const StepGeom& G, uint64_t i, uint64_t nl, uint6
 
 // ------------------------------------------------------------ parameter rule
 // Chooses the line size b and the group count g of one step on n keys of
-// key_bytes each, for a grid of `ctas` CTAs and lines of at most
-// line_bytes_max bytes.  Large ranges get the largest
-// line that still leaves at least kMinChunks chunks with one group per CTA;
-// a range of at most kFinishBytes (or that cannot feed two groups) is one
-// group, i.e. a plain CTA-wide partition (the paper's base case).
+// key_bytes each, for `groups_max` concurrent group workers (warps) and lines
+// of at most line_bytes_max bytes.  Large ranges get the largest line that
+// still leaves at least kMinChunks chunks with one group per worker; smaller
+// ranges get shorter lines, then fewer groups.  g == 0 means: at most
+// finish_keys keys, which one CTA partitions in shared memory (the paper's
+// base case).
 struct StepParams { uint64_t b, g; };
 
-LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t ctas,
-                               uint32_t line_bytes_max) {
+LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t groups_max,
+                               uint32_t line_bytes_max, uint64_t finish_keys) {
   StepParams P;
   P.b = line_bytes_max / key_bytes;
-  P.g = 1;
-  if (n * key_bytes <= kFinishBytes || ctas < 2) return P;
+  P.g = 0;
+  if (n <= finish_keys) return P;
   for (uint32_t lb = line_bytes_max; lb >= kLineBytesMin; lb >>= 1) {
-    uint64_t b = lb / key_bytes;
-    uint64_t g = n / (b * kMinChunks);
+    const uint64_t b = lb / key_bytes;
+    const uint64_t g = n / (b * kMinChunks);
     P.b = b;
     P.g = g;
-    if (g >= ctas) { P.g = ctas; return P; }
+    if (g >= groups_max) { P.g = groups_max; return P; }
   }
-  if (P.g < 2) P.g = 1;
+  if (P.g < 2) P.g = 2;
   return P;
 }
 
@@ -180,5 +186,34 @@ LP_HD bool ctl_consumed(const StreamCtl& c, int64_t line) {
 }
 LP_HD uint64_t ctl_p_count(const StreamCtl& c) { return c.p_tail - c.p_head; }
 LP_HD uint64_t ctl_s_count(const StreamCtl& c) { return c.s_tail - c.s_head; }
+
+// Picks up to maxw lines for the next batch with the slack policy, marking
+// them consumed.  For each: the line, whether it was loaded from the front
+// queue, and its stage.  Returns the number picked (0 once all are consumed).
+LP_HD uint32_t ctl_pick_batch(StreamCtl& c, uint32_t maxw, int64_t* lines, bool* from_front,
+                              uint32_t* stages) {
+  uint32_t w = 0;
+  while (w < maxw && !ctl_done(c)) {
+    const bool front = ctl_pick_front(c);
+    const int64_t line = front ? c.lo_c : c.hi_c;
+    lines[w] = line;
+    from_front[w] = line < c.fi;
+    stages[w] = ctl_stage_of(c, line);
+    if (front) c.lo_c++; else c.hi_c--;
+    w++;
+  }
+  return w;
+}
+
+// Slot of a line in the per-CTA table of (line, length) records:
+// front-issued lines in [0, kLineTab), back-issued in [kLineTab, 2 kLineTab).
+LP_HD uint32_t line_tab_slot_side(const StreamCtl& c, int64_t line, bool front) {
+  return front ? (uint32_t)(line % kLineTab)
+               : kLineTab + (uint32_t)((c.nl - 1 - line) % kLineTab);
+}
+// Same for a line already issued (lines below fi came from the front).
+LP_HD uint32_t line_tab_slot(const StreamCtl& c, int64_t line) {
+  return line_tab_slot_side(c, line, line < c.fi);
+}
 
 }  // namespace lp

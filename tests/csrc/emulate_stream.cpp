@@ -46,7 +46,8 @@ static bool overlaps(uint64_t a0, uint64_t alen, uint64_t b0, uint64_t blen, uin
 
 // lines: nl lines of b keys, the last of length last_len; keys are 0/1 flags
 // (1 = predecessor).
-static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uint64_t ring_keys) {
+static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uint64_t ring_keys,
+                     uint32_t maxw) {
   std::vector<std::vector<int>> line(nl);
   for (int64_t m = 0; m < nl; m++) {
     uint64_t len = (m == nl - 1) ? last_len : b;
@@ -87,8 +88,10 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uin
   StreamCtl c;
   ctl_init(c, nl);
   uint32_t phase = 0;
+  // issued-line table, as in the kernel: slot -> line (checks validity)
+  std::vector<int64_t> tab(2 * kLineTab, -1);
 
-  auto issue = [&](int64_t m, uint32_t st) {
+  auto issue = [&](int64_t m, uint32_t st, bool front) {
     CHECK(m >= 0 && m < nl, "issue out of range %lld", (long long)m);
     CHECK(!loaded[m], "line %lld loaded twice", (long long)m);
     CHECK(!stage_busy[st], "stage %u refilled before consumption", st);
@@ -98,10 +101,16 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uin
     stage_data[st] = line[m];
     stage_done_parity[st] = stage_completions[st] & 1u;  // parity of this completion
     stage_completions[st]++;
+    tab[line_tab_slot_side(c, m, front)] = m;
+  };
+  auto tab_check = [&](int64_t m) {
+    CHECK(tab[line_tab_slot(c, m)] == m, "line table slot of line %lld overwritten",
+          (long long)m);
   };
   auto do_flush = [&](int ring, uint64_t head, int64_t m) {
     CHECK(ctl_consumed(c, m), "flush into unconsumed line %lld", (long long)m);
     CHECK(!written[m], "line %lld written twice", (long long)m);
+    tab_check(m);
     written[m] = 1;
     std::vector<int>& r = ring ? sring : pring;
     for (uint64_t q = 0; q < line[m].size(); q++) line[m][q] = r[(head + q) % ring_keys];
@@ -109,45 +118,56 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uin
   };
 
   for (uint32_t q = 0; q < kQ; q++) {
-    if (ctl_can_issue(c)) { issue(c.fi, stage_front(c.fi)); c.fi++; }
-    if (ctl_can_issue(c)) { issue(c.bi, stage_back(c, c.bi)); c.bi--; }
+    if (ctl_can_issue(c)) { issue(c.fi, stage_front(c.fi), true); c.fi++; }
+    if (ctl_can_issue(c)) { issue(c.bi, stage_back(c, c.bi), false); c.bi--; }
   }
-  while (!ctl_done(c)) {
-    const bool front = ctl_pick_front(c);
-    const int64_t m = front ? c.lo_c : c.hi_c;
-    const bool from_front_q = m < c.fi;
-    const uint32_t st = ctl_stage_of(c, m);
-    const uint64_t len = line[m].size();
-    CHECK(ctl_p_count(c) + len + kPendingFlushes * b <= ring_keys, "P ring bound");
-    CHECK(ctl_s_count(c) + len + kPendingFlushes * b <= ring_keys, "S ring bound");
-    CHECK(stage_busy[st] && stage_line[st] == m, "stage %u does not hold line %lld", st,
-          (long long)m);
-    CHECK(((phase >> st) & 1u) == stage_done_parity[st], "parity mismatch at stage %u", st);
-    // classify: append (checking pending regions)
-    uint64_t np = 0;
-    for (int v : stage_data[st]) np += v;
-    for (auto& f : pending) {
-      if (f.ring == 0)
-        CHECK(!overlaps(c.p_tail, np, f.head, f.len, ring_keys), "P append over pending flush");
-      else
-        CHECK(!overlaps(c.s_tail, len - np, f.head, f.len, ring_keys),
-              "S append over pending flush");
+  int64_t cur[kBatchMax];
+  bool cur_ff[kBatchMax];
+  uint32_t sts[kBatchMax];
+  uint32_t n = ctl_pick_batch(c, maxw, cur, cur_ff, sts);
+  uint32_t par[kBatchMax];
+  for (uint32_t j = 0; j < n; j++) { par[j] = (phase >> sts[j]) & 1u; phase ^= 1u << sts[j]; }
+  while (n > 0) {
+    // workers: wait, classify, append in batch order
+    uint64_t np_tot = 0, ns_tot = 0;
+    for (uint32_t j = 0; j < n; j++) {
+      const int64_t m = cur[j];
+      const uint32_t st = sts[j];
+      tab_check(m);
+      CHECK(stage_busy[st] && stage_line[st] == m, "stage %u does not hold line %lld", st,
+            (long long)m);
+      CHECK(par[j] == stage_done_parity[st], "parity mismatch at stage %u", st);
+      uint64_t np = 0;
+      for (int v : stage_data[st]) np += v;
+      uint64_t ns = stage_data[st].size() - np;
+      for (auto& f : pending) {
+        if (f.ring == 0)
+          CHECK(!overlaps(c.p_tail + np_tot, np, f.head, f.len, ring_keys), "P append over pending");
+        else
+          CHECK(!overlaps(c.s_tail + ns_tot, ns, f.head, f.len, ring_keys), "S append over pending");
+      }
+      // the batch never overruns the unread part of its own ring
+      CHECK(ctl_p_count(c) + np_tot + np <= ring_keys, "P ring overrun");
+      CHECK(ctl_s_count(c) + ns_tot + ns <= ring_keys, "S ring overrun");
+      uint64_t pp = c.p_tail + np_tot, sp = c.s_tail + ns_tot;
+      for (int v : stage_data[st]) {
+        if (v) pring[(pp++) % ring_keys] = v; else sring[(sp++) % ring_keys] = v;
+      }
+      np_tot += np;
+      ns_tot += ns;
+      stage_busy[st] = 0;
     }
-    uint64_t pp = c.p_tail, sp = c.s_tail;
-    for (int v : stage_data[st]) {
-      if (v) pring[(pp++) % ring_keys] = v; else sring[(sp++) % ring_keys] = v;
-    }
-    phase ^= 1u << st;
-    stage_busy[st] = 0;
-    c.p_tail += np;
-    c.s_tail += len - np;
-    c.k += np;
-    if (front) c.lo_c++; else c.hi_c--;
-    if (ctl_can_issue(c)) {
-      if (from_front_q) { issue(c.fi, stage_front(c.fi)); c.fi++; }
-      else { issue(c.bi, stage_back(c, c.bi)); c.bi--; }
+    // thread 0: bookkeeping, refills, write-back plan, next batch
+    c.p_tail += np_tot;
+    c.s_tail += ns_tot;
+    c.k += np_tot;
+    for (uint32_t j = 0; j < n; j++) {
+      if (!ctl_can_issue(c)) break;
+      if (cur_ff[j]) { issue(c.fi, stage_front(c.fi), true); c.fi++; }
+      else { issue(c.bi, stage_back(c, c.bi), false); c.bi--; }
     }
     while (c.fw <= c.bw && ctl_consumed(c, c.fw)) {
+      tab_check(c.fw);
       uint64_t lw = line[c.fw].size();
       if (ctl_p_count(c) < lw) break;
       do_flush(0, c.p_head, c.fw);
@@ -155,12 +175,18 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uin
       c.fw++;
     }
     while (c.bw >= c.fw && ctl_consumed(c, c.bw)) {
+      tab_check(c.bw);
       uint64_t lw = line[c.bw].size();
       if (ctl_s_count(c) < lw) break;
       do_flush(1, c.s_head, c.bw);
       c.s_head += lw;
       c.bw--;
     }
+    const uint64_t need = (uint64_t)(maxw + kPendingFlushes) * b;
+    CHECK(ctl_p_count(c) + need <= ring_keys, "P ring bound (kernel check would abort)");
+    CHECK(ctl_s_count(c) + need <= ring_keys, "S ring bound (kernel check would abort)");
+    n = ctl_pick_batch(c, maxw, cur, cur_ff, sts);
+    for (uint32_t j = 0; j < n; j++) { par[j] = (phase >> sts[j]) & 1u; phase ^= 1u << sts[j]; }
     while (pending.size() > kPendingFlushes) pending.pop_front();
   }
   // remainder
@@ -175,6 +201,7 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uin
   for (uint64_t q = 0; q < rem; q++) {
     int v = q < pc ? pring[(c.p_head + q) % ring_keys] : sring[(c.s_head + q - pc) % ring_keys];
     int64_t m = c.fw + (int64_t)(q / b);
+    tab_check(m);
     line[m][q % b] = v;
     written[m] = 1;
   }
@@ -194,15 +221,22 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern, uin
 int main(int argc, char** argv) {
   int cases = argc > 1 ? atoi(argv[1]) : 2000;
   rs ^= argc > 2 ? strtoull(argv[2], 0, 10) * 0x9E3779B97F4A7C15ull : 0;
-  const uint64_t bs[] = {4, 8, 16, 64, 512};
+  // line sizes in 16-byte vectors, as the kernel maps them: 2048-byte lines
+  // (the largest) down to 512-byte lines; keys per vector 2 (u64) or 4 (u32)
+  // per-warp geometry of the kernel: the largest line is 512 key bytes (32
+  // vectors); levels use lines down to 128 bytes (8 vectors); rings hold 8
+  // lines of the largest size; one line per step.
   for (int t = 0; t < cases; t++) {
-    uint64_t b = bs[rnd() % 5];
-    int64_t nl = 1 + (int64_t)(rnd() % (t % 3 == 0 ? 300 : 24));
+    const uint32_t max_lv = 32;
+    uint32_t lv = max_lv >> (rnd() % 3);
+    uint32_t kpv = (rnd() & 1) ? 2 : 4;
+    uint64_t b = (uint64_t)lv * kpv;
+    int64_t nl = 1 + (int64_t)(rnd() % (t % 3 == 0 ? 400 : 30));
     uint64_t last = b;
-    if (rnd() % 2) last = 1 + rnd() % b;
+    if (rnd() % 2) last = kpv * (1 + rnd() % lv);  // partial last line, whole vectors
     int pattern = (int)(rnd() % 9);
-    uint64_t ring = 8 * b;  // ring holds 8 full lines, as in the kernel
-    run_case(nl, b, last, pattern, ring);
+    uint64_t ring = (uint64_t)kRingLines * max_lv * kpv;
+    run_case(nl, b, last, pattern, ring, kBatchMax);
   }
   printf("OK\n");
   return 0;

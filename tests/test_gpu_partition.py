@@ -49,8 +49,9 @@ def group_of_positions(n, b, g, X):
 
 @pytest.mark.parametrize("n,b,g,strided", [
     (1 << 16, 64, 16, 0), (1 << 16, 64, 16, 1), (100000, 32, 37, 0),
-    (1 << 20, 512, 304, 0), ((1 << 20) + 4096 + 2, 256, 100, 0), (4096, 8, 3, 0),
-    (2 * 1000, 2, 7, 0), (5000, 512, 3, 0), (30000, 16, 1, 0)])
+    (1 << 20, 64, 304, 0), ((1 << 20) + 4096 + 2, 64, 100, 0), (4096, 8, 3, 0),
+    (2 * 1000, 2, 7, 0), (5000, 64, 3, 0), (30000, 16, 1, 0), (1 << 20, 64, 3000, 0),
+    ((1 << 22) + 18, 32, 2000, 0), (1 << 21, 64, 1, 0), (1 << 22, 64, 2432, 1)])
 def test_step_parity(ctx, n, b, g, strided):
     """One Partial Partition Step: v_min, v_max and the count equal the
     oracle's for the same X; every group is a predecessors-first permutation
@@ -82,7 +83,7 @@ def test_step_parity(ctx, n, b, g, strided):
 
 
 def test_step_u32(ctx):
-    n, b, g = 1 << 18, 1024, 50
+    n, b, g = 1 << 18, 128, 50
     host = inputs.uniform_u32(n, 5)
     pv = inputs.quantile_pivot(1, 3, 32)
     dev = to_dev(host)
@@ -102,6 +103,9 @@ def test_step_rejects_bad_args(ctx):
     assert e.value.status == lp.LP_ERR_MISALIGNED
     with pytest.raises(lp.LPError) as e:
         lp.lp_smoothed_step(ctx, dev, P50, 3, 4)  # 24-byte line
+    assert e.value.status == lp.LP_ERR_INVALID_ARG
+    with pytest.raises(lp.LPError) as e:
+        lp.lp_smoothed_step(ctx, dev, P50, 128, 4)  # 1024-byte line: above the limit
     assert e.value.status == lp.LP_ERR_INVALID_ARG
 
 
