@@ -137,7 +137,7 @@ lp_status lp_partition_kv_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t *vals,
  * has none); *count = number of predecessors.  Afterwards keys[p] <= pivot
  * for p < vmin and keys[p] > pivot for p >= vmax.
  * Requires keys 16-byte aligned, n * sizeof(key) and b * sizeof(key)
- * multiples of 16, b * sizeof(key) <= 512, g >= 1; otherwise
+ * multiples of 16, b * sizeof(key) <= 1024, g >= 1; otherwise
  * LP_ERR_MISALIGNED / LP_ERR_INVALID_ARG.  Synchronises `stream`. */
 lp_status lp_smoothed_step_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
                                uint64_t b, uint64_t g, uint64_t seed, uint64_t level,

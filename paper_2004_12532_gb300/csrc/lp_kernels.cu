@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint
   for (uint64_t i = gw; i < G.g; i += total_warps) {
     const int64_t nl = (int64_t)group_num_lines(G, i);
     uint64_t k = 0;
-    if (!warp_stream_group<T, KV>(base, vbase, G, i, nl, pivot, ws, phase, k, status)) break;
+    if (!warp_pair_group<T, KV>(base, vbase, G, i, nl, pivot, ws, phase, k, status)) break;
     if (nl > 0 && lane == 0) {
       const unsigned long long v = lo + group_split_pos(G, i, (uint64_t)nl, k);
       atomicMin(&out->vmin, v);
@@ -119,7 +119,6 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint
       atomicAdd(&out->count, (unsigned long long)k);
     }
   }
-  if (lane == 0) bulk_wait_all<0>();
 }
 
 // Head keys [0, h) and tail keys [body_end, n) lie outside the 16-byte aligned

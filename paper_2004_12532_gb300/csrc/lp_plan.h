@@ -20,17 +20,13 @@ namespace lp {
 
 // ---------------------------------------------------------------- constants
 // The streaming kernels give one warp one group (the paper's "serial
-// partition of U_i", one processor per group).  Per warp: kQ line loads in
-// flight per side, two rings (P, S) of kRingLines lines, bulk stores allowed
-// to read smem for up to kPendingFlushes write-backs.
-constexpr uint32_t kLineBytesMax = 512;    // largest line (stage) in key bytes
+// partition of U_i", one processor per group).  A warp holds two lines of its
+// group in registers (the paper's `low` and `high` ends) and keeps kQ more
+// lines in flight per side in shared memory.
+constexpr uint32_t kLineBytesMax = 1024;   // largest line in key bytes (2 vectors per lane)
 constexpr uint32_t kLineBytesMin = 128;    // smallest line used by the parameter rule
 constexpr uint32_t kQ = 4;                 // loads in flight per side (front / back)
 constexpr uint32_t kStages = 2 * kQ;       // input stages per warp
-constexpr uint32_t kRingLines = 8;         // ring capacity, in lines of the largest size
-constexpr uint32_t kPendingFlushes = 2;    // bulk stores allowed to still read smem
-constexpr uint32_t kLineTab = 16;          // issued-line table entries per side
-constexpr uint32_t kBatchMax = 1;          // lines consumed per step
 constexpr uint32_t kFinishBytes = 64 * 1024;  // ranges up to this size: one CTA in smem
 constexpr uint32_t kMinChunks = 64;        // s at least this large when g > 1
 
@@ -147,73 +143,34 @@ LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t groups_m
   return P;
 }
 
-// ------------------------------------------------- streaming control state
-// One CTA partitions one group as a stream of its nl lines (in group order):
-// lines are loaded from both ends (kQ in flight per side), every consumed
-// line's predecessors go to ring P and successors to ring S, and a full
-// line's worth of P (S) is written back to the lowest (highest) unwritten
-// line once that line has been consumed.  Each line is read once and written
-// once; the last one or two lines take what is left in the rings, P first.
-struct StreamCtl {
-  int64_t nl;            // lines in the group
-  int64_t fi, bi;        // next line to load from the front / the back
-  int64_t lo_c, hi_c;    // lowest / highest line not yet consumed
-  int64_t fw, bw;        // next line to receive P (front) / S (back)
-  uint64_t p_head, p_tail, s_head, s_tail;  // ring counters, in keys
-  uint64_t k;            // predecessors seen
+// --------------------------------------------- line-pair (Hoare) control
+// A warp partitions its group as the paper's serial two-pointer scan does,
+// one line at a time instead of one key: it holds the lowest unfinished line
+// L and the highest unfinished line R, swaps the j-th successor of L with the
+// j-th predecessor of R for j < min(#succ(L), #pred(R)), and writes back
+// whichever line became pure (L all predecessors, or R all successors; both
+// when the counts match), then takes the next line from that side.  When no
+// unread line is left, the line still in hand is partitioned on its own.
+// Lines are loaded ahead from both ends, kQ per side; `fi` / `bi` are the next
+// lines to load from the front / back, [fnext, bnext] the lines not yet taken.
+struct PairCtl {
+  int64_t nl;          // lines in the group
+  int64_t fi, bi;      // next line to load from the front / the back
+  int64_t fnext, bnext;  // lines not yet taken: [fnext, bnext]
 };
 
-LP_HD void ctl_init(StreamCtl& c, int64_t nl) {
-  c.nl = nl; c.fi = 0; c.bi = nl - 1; c.lo_c = 0; c.hi_c = nl - 1;
-  c.fw = 0; c.bw = nl - 1; c.p_head = c.p_tail = c.s_head = c.s_tail = 0; c.k = 0;
+LP_HD void pair_init(PairCtl& c, int64_t nl) {
+  c.nl = nl; c.fi = 0; c.bi = nl - 1; c.fnext = 0; c.bnext = nl - 1;
 }
-LP_HD bool ctl_can_issue(const StreamCtl& c) { return c.fi <= c.bi; }
-LP_HD bool ctl_done(const StreamCtl& c) { return c.lo_c > c.hi_c; }
-LP_HD uint32_t stage_front(int64_t line) { return (uint32_t)(line % kQ); }
-LP_HD uint32_t stage_back(const StreamCtl& c, int64_t line) {
+LP_HD bool pair_can_issue(const PairCtl& c) { return c.fi <= c.bi; }
+LP_HD uint32_t pair_stage_front(int64_t line) { return (uint32_t)(line % kQ); }
+LP_HD uint32_t pair_stage_back(const PairCtl& c, int64_t line) {
   return kQ + (uint32_t)((c.nl - 1 - line) % kQ);
 }
-// Stage holding an issued line: lines below fi came from the front.
-LP_HD uint32_t ctl_stage_of(const StreamCtl& c, int64_t line) {
-  return line < c.fi ? stage_front(line) : stage_back(c, line);
+// Stage holding an issued line: lines below fi came from the front queue.
+LP_HD uint32_t pair_stage_of(const PairCtl& c, int64_t line) {
+  return line < c.fi ? pair_stage_front(line) : pair_stage_back(c, line);
 }
-// Consume from the side whose written-behind slack is smaller (ties: front).
-LP_HD bool ctl_pick_front(const StreamCtl& c) {
-  return (c.lo_c - c.fw) <= (c.bw - c.hi_c);
-}
-LP_HD bool ctl_consumed(const StreamCtl& c, int64_t line) {
-  return line < c.lo_c || line > c.hi_c;
-}
-LP_HD uint64_t ctl_p_count(const StreamCtl& c) { return c.p_tail - c.p_head; }
-LP_HD uint64_t ctl_s_count(const StreamCtl& c) { return c.s_tail - c.s_head; }
-
-// Picks up to maxw lines for the next batch with the slack policy, marking
-// them consumed.  For each: the line, whether it was loaded from the front
-// queue, and its stage.  Returns the number picked (0 once all are consumed).
-LP_HD uint32_t ctl_pick_batch(StreamCtl& c, uint32_t maxw, int64_t* lines, bool* from_front,
-                              uint32_t* stages) {
-  uint32_t w = 0;
-  while (w < maxw && !ctl_done(c)) {
-    const bool front = ctl_pick_front(c);
-    const int64_t line = front ? c.lo_c : c.hi_c;
-    lines[w] = line;
-    from_front[w] = line < c.fi;
-    stages[w] = ctl_stage_of(c, line);
-    if (front) c.lo_c++; else c.hi_c--;
-    w++;
-  }
-  return w;
-}
-
-// Slot of a line in the per-CTA table of (line, length) records:
-// front-issued lines in [0, kLineTab), back-issued in [kLineTab, 2 kLineTab).
-LP_HD uint32_t line_tab_slot_side(const StreamCtl& c, int64_t line, bool front) {
-  return front ? (uint32_t)(line % kLineTab)
-               : kLineTab + (uint32_t)((c.nl - 1 - line) % kLineTab);
-}
-// Same for a line already issued (lines below fi came from the front).
-LP_HD uint32_t line_tab_slot(const StreamCtl& c, int64_t line) {
-  return line_tab_slot_side(c, line, line < c.fi);
-}
+LP_HD bool pair_has_unread(const PairCtl& c) { return c.fnext <= c.bnext; }
 
 }  // namespace lp

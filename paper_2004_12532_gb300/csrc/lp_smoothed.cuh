@@ -4,24 +4,23 @@
 //
 // GPU mapping.  Each warp owns one group U_i at a time (the paper partitions
 // every U_i serially, one processor per group).  The group's lines -- line
-// j*g + (X[j]+i) mod g of every chunk j -- form a stream of nl lines in group
-// order, which the warp partitions in place:
-//   * lane 0 loads lines with 1-D bulk asynchronous copies (TMA) from both
-//     ends of the stream, kQ lines in flight per side, each completing on an
-//     mbarrier;
-//   * every lane classifies one 16-byte vector of the consumed line; warp
-//     ballots give each key its rank, and keys are appended to one of two
-//     shared-memory rings (P: predecessors, S: successors);
-//   * a full line of P is written back (bulk store) to the lowest line of the
-//     stream not yet written, a full line of S to the highest, and only into
-//     lines already consumed; the last one or two lines take what is left,
-//     P first.
-// Which end to consume next is decided by the slack of written-back lines on
-// each side (lp_plan.h, StreamCtl), which keeps both rings bounded for any
-// input.  Every line is read once and written once: one read and one write of
-// every key, the I/O of the paper's Prop. 4.2.  The group ends predecessors
-// first in its own slot order, exactly as the paper's serial partition leaves
-// it, so k_i and v_i are the paper's.
+// j*g + (X[j]+i) mod g of every chunk j -- form a sequence of nl lines in
+// group order, which the warp partitions in place with the paper's serial
+// two-pointer scan taken one line at a time:
+//   * the warp holds the lowest unfinished line L and the highest unfinished
+//     line R in registers (lane l holds vectors l and 32+l of each);
+//   * the j-th successor of L and the j-th predecessor of R are swapped for
+//     j < min(#successors(L), #predecessors(R)) -- ranks come from warp
+//     ballots, the keys cross through a small shared-memory buffer;
+//   * whichever line became pure (L all predecessors, R all successors) is
+//     written straight back with coalesced 16-byte stores, and the next line
+//     of that side is taken; the last line left is partitioned on its own;
+//   * lane 0 keeps kQ lines per side in flight with 1-D bulk asynchronous
+//     copies (TMA) into shared-memory stages, each completing on an mbarrier.
+// Every line is read once and written once: one read and one write of every
+// key, the I/O of the paper's Prop. 4.2.  The group ends predecessors first in
+// its own slot order, as the paper's serial partition leaves it, so k_i and
+// v_i are the paper's.
 //
 // The random offsets X[j] are computed 32 at a time, one per lane, and
 // fetched by shuffle.  v_min / v_max are reduced with 64-bit atomic min / max
@@ -60,9 +59,9 @@ struct Tr {
   static constexpr uint32_t K = sizeof(T);
   static constexpr uint32_t LineBytes = kLineBytesMax;          // key bytes per line, max
   static constexpr uint32_t LineKeys = LineBytes / K;
-  static constexpr uint32_t RingKeys = kRingLines * LineKeys;   // power of two
   static constexpr uint32_t V = 16u / K;                        // keys per 16-byte vector
   static constexpr uint32_t A = 16u / K;                        // alignment unit in keys
+  static constexpr uint32_t VPL = LineBytes / 16u / 32u;        // vectors per lane per line
   static constexpr uint32_t Warps = KV ? 4u : 8u;               // groups in flight per CTA
   static constexpr uint32_t Threads = 32u * Warps;
   // one CTA partitions ranges up to this many keys in shared memory
@@ -72,14 +71,12 @@ struct Tr {
 template <typename T, bool KV>
 struct __align__(128) WarpSmem {
   T stage[kStages][Tr<T, KV>::LineKeys];
-  T pring[Tr<T, KV>::RingKeys];
-  T sring[Tr<T, KV>::RingKeys];
+  T xbuf[2][Tr<T, KV>::LineKeys];
   uint64_t vstage[KV ? kStages : 1][KV ? Tr<T, KV>::LineKeys : 2];
-  uint64_t vpring[KV ? Tr<T, KV>::RingKeys : 2];
-  uint64_t vsring[KV ? Tr<T, KV>::RingKeys : 2];
+  uint64_t vxbuf[KV ? 2 : 1][KV ? Tr<T, KV>::LineKeys : 2];
   uint64_t bar[kStages];
-  uint32_t tab_line[2 * kLineTab];   // issued lines: line index within the range
-  uint32_t tab_len[2 * kLineTab];    // ... and its length in keys
+  uint32_t st_line[kStages];   // line (within the range) loaded into each stage
+  uint32_t st_len[kStages];    // ... and its length in keys
 };
 
 template <typename T, bool KV>
@@ -100,20 +97,39 @@ __device__ __forceinline__ void load_vec(const T* p, T (&x)[16 / sizeof(T)]) {
   }
 }
 
+template <typename T>
+__device__ __forceinline__ void store_vec(T* p, const T (&x)[16 / sizeof(T)]) {
+  if constexpr (sizeof(T) == 8) {
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x[0], x[1]);
+  } else {
+    *reinterpret_cast<uint4*>(p) = make_uint4(x[0], x[1], x[2], x[3]);
+  }
+}
+
+// One line of a group in registers: lane l holds vectors u*32 + l, u < VPL.
+template <typename T, bool KV>
+struct LineReg {
+  T x[Tr<T, KV>::VPL][Tr<T, KV>::V];
+  uint64_t y[KV ? Tr<T, KV>::VPL : 1][KV ? Tr<T, KV>::V : 1];
+  uint32_t pred;   // bit u*V+v: key (u, v) is a predecessor
+  uint32_t valid;  // bit u: vector u*32 + lane exists
+  uint32_t gl;     // line index within the range (warp-uniform)
+  uint32_t len;    // keys in the line (warp-uniform)
+};
+
 // Partition group i of step G over the range starting at `base` (`vbase`
 // for payloads).  Called by all 32 lanes of one warp with the same arguments;
 // control is warp-uniform, lane 0 issues the bulk copies.  `phase` holds one
 // parity bit per stage and persists across the warp's groups.  Returns false
-// if a bounded wait gave up or a ring check failed (after draining the warp's
-// copies in flight); k receives the group's predecessor count.
+// if a bounded wait gave up (after draining the warp's copies in flight);
+// k receives the group's predecessor count.
 template <typename T, bool KV>
-__device__ bool warp_stream_group(T* __restrict__ base, uint64_t* __restrict__ vbase,
-                                  const StepGeom& G, uint64_t i, int64_t nl, T pivot,
-                                  WarpSmem<T, KV>& sm, uint32_t& phase, uint64_t& k,
-                                  uint32_t* status) {
+__device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vbase,
+                                const StepGeom& G, uint64_t i, int64_t nl, T pivot,
+                                WarpSmem<T, KV>& sm, uint32_t& phase, uint64_t& k,
+                                uint32_t* status) {
   using R = Tr<T, KV>;
-  constexpr uint32_t MASK = R::RingKeys - 1;
-  constexpr uint32_t V = R::V;
+  constexpr uint32_t V = R::V, VPL = R::VPL;
   constexpr uint32_t FULL = 0xffffffffu;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -142,8 +158,8 @@ __device__ bool warp_stream_group(T* __restrict__ base, uint64_t* __restrict__ v
     return __shfl_sync(FULL, xb, (int)(wb - m));
   };
 
-  StreamCtl c;
-  ctl_init(c, nl);
+  PairCtl c;
+  pair_init(c, nl);
 
   auto issue = [&](int64_t line, uint32_t st, bool front) {
     const uint64_t x = front ? x_front(line) : x_back(line);
@@ -152,160 +168,188 @@ __device__ bool warp_stream_group(T* __restrict__ base, uint64_t* __restrict__ v
     const uint64_t gl = (uint64_t)line * G.g + off;
     const uint32_t len = (uint32_t)line_len(G, gl);
     if (lane == 0) {
-      const uint32_t slot = line_tab_slot_side(c, line, front);
-      sm.tab_line[slot] = (uint32_t)gl;
-      sm.tab_len[slot] = len;
+      sm.st_line[st] = (uint32_t)gl;
+      sm.st_len[st] = len;
       const uint32_t bytes = len * R::K;
       mbar_arrive_expect_tx(&sm.bar[st], KV ? 2u * bytes : bytes);
       bulk_load(&sm.stage[st][0], base + gl * G.b, bytes, &sm.bar[st]);
       if constexpr (KV) bulk_load(&sm.vstage[st][0], vbase + gl * G.b, bytes, &sm.bar[st]);
     }
   };
-  auto flush = [&](const T* ring, const uint64_t* vring, uint64_t head, uint32_t gl,
-                   uint32_t len) {
-    // lane 0: ring[head .. head+len) -> line gl, split at the ring end
-    const uint32_t off = (uint32_t)(head & MASK);
-    const uint32_t first = min(len, R::RingKeys - off);
-    T* dst = base + (uint64_t)gl * G.b;
-    bulk_store(dst, ring + off, first * R::K);
-    if constexpr (KV) bulk_store(vbase + (uint64_t)gl * G.b, vring + off, first * 8u);
-    if (first < len) {
-      bulk_store(dst + first, ring, (len - first) * R::K);
-      if constexpr (KV) bulk_store(vbase + (uint64_t)gl * G.b + first, vring, (len - first) * 8u);
-    }
-    bulk_commit();
-  };
-
-  for (uint32_t q = 0; q < kQ; q++) {
-    if (ctl_can_issue(c)) { issue(c.fi, stage_front(c.fi), true); c.fi++; }
-    if (ctl_can_issue(c)) { issue(c.bi, stage_back(c, c.bi), false); c.bi--; }
-  }
-  __syncwarp();
-
-  bool ok = true;
-  while (!ctl_done(c)) {
-    const bool front = ctl_pick_front(c);
-    const int64_t line = front ? c.lo_c : c.hi_c;
-    const bool from_front_q = line < c.fi;
-    const uint32_t st = ctl_stage_of(c, line);
-    const uint32_t len = sm.tab_len[line_tab_slot(c, line)];
-
-    // ring capacity, counting bulk stores that may still read (uniform)
-    if (ctl_p_count(c) + len + kPendingFlushes * G.b > R::RingKeys ||
-        ctl_s_count(c) + len + kPendingFlushes * G.b > R::RingKeys) {
-      if (lane == 0) atomicOr(status, kStatRing);
-      ok = false;
-      break;
-    }
+  // take an issued line into registers; refill its stage; false on timeout
+  auto take = [&](int64_t line, LineReg<T, KV>& Lr) -> bool {
+    const uint32_t st = pair_stage_of(c, line);
+    const bool front_stage = st < kQ;
     const bool arrived = mbar_wait_bounded(&sm.bar[st], (phase >> st) & 1u);
-    if (!__all_sync(FULL, arrived)) {
-      if (lane == 0) atomicOr(status, kStatTimeout);
-      ok = false;
-      break;
-    }
+    if (!__all_sync(FULL, arrived)) return false;
     phase ^= 1u << st;
-
-    // classify: lane l takes vector l of the line
-    const bool act = lane < len / V;
-    T x[V];
-    uint64_t y[V];
-    uint32_t flags = 0;
-    if (act) {
-      load_vec<T>(&sm.stage[st][lane * V], x);
-      if constexpr (KV) {
-        const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&sm.vstage[st][lane * V]);
-        y[0] = w.x; y[1] = w.y;
+    Lr.gl = sm.st_line[st];
+    Lr.len = sm.st_len[st];
+    const uint32_t nvec = Lr.len / V;
+    Lr.pred = 0;
+    Lr.valid = 0;
+#pragma unroll
+    for (uint32_t u = 0; u < VPL; u++) {
+      const uint32_t vec = u * 32u + lane;
+      if (vec < nvec) {
+        Lr.valid |= 1u << u;
+        load_vec<T>(&sm.stage[st][vec * V], Lr.x[u]);
+        if constexpr (KV) {
+          const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&sm.vstage[st][vec * V]);
+          Lr.y[u][0] = w.x; Lr.y[u][1] = w.y;
+        }
+#pragma unroll
+        for (uint32_t v = 0; v < V; v++)
+          Lr.pred |= (Lr.x[u][v] <= pivot ? 1u : 0u) << (u * V + v);
       }
-#pragma unroll
-      for (uint32_t v = 0; v < V; v++) flags |= (x[v] <= pivot ? 1u : 0u) << v;
     }
-    uint32_t np = 0, pl = 0;
-#pragma unroll
-    for (uint32_t v = 0; v < V; v++) {
-      const uint32_t bv = __ballot_sync(FULL, (flags >> v) & 1u);
-      np += __popc(bv);
-      pl += __popc(bv & lt);
+    k += (uint64_t)__reduce_add_sync(FULL, __popc(Lr.pred));
+    __syncwarp();  // every lane has read the stage: it may be refilled
+    if (pair_can_issue(c)) {
+      if (front_stage) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
+      else { issue(c.bi, pair_stage_back(c, c.bi), false); c.bi--; }
     }
-    if (act) {
-      const uint32_t kl = lane * V;  // keys of the lanes below (all full vectors)
-      uint64_t pp = c.p_tail + pl;
-      uint64_t sp = c.s_tail + (kl - pl);
+    return true;
+  };
+  auto store_line = [&](const LineReg<T, KV>& Lr) {
+    T* dst = base + (uint64_t)Lr.gl * G.b;
 #pragma unroll
-      for (uint32_t v = 0; v < V; v++) {
-        if ((flags >> v) & 1u) {
-          sm.pring[pp & MASK] = x[v];
-          if constexpr (KV) sm.vpring[pp & MASK] = y[v];
-          pp++;
-        } else {
-          sm.sring[sp & MASK] = x[v];
-          if constexpr (KV) sm.vsring[sp & MASK] = y[v];
-          sp++;
+    for (uint32_t u = 0; u < VPL; u++) {
+      if ((Lr.valid >> u) & 1u) {
+        const uint32_t vec = u * 32u + lane;
+        store_vec<T>(dst + vec * V, Lr.x[u]);
+        if constexpr (KV) {
+          *reinterpret_cast<ulonglong2*>(vbase + (uint64_t)Lr.gl * G.b + vec * V) =
+              make_ulonglong2(Lr.y[u][0], Lr.y[u][1]);
         }
       }
     }
-    fence_proxy_async_smem();
-    __syncwarp();  // ring writes visible to the copy engine; the stage is free
+  };
 
-    c.p_tail += np;
-    c.s_tail += len - np;
-    c.k += np;
-    if (front) c.lo_c++; else c.hi_c--;
+  for (uint32_t q = 0; q < kQ; q++) {
+    if (pair_can_issue(c)) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
+    if (pair_can_issue(c)) { issue(c.bi, pair_stage_back(c, c.bi), false); c.bi--; }
+  }
+  __syncwarp();
 
-    // refill the freed stage from the side it served
-    if (ctl_can_issue(c)) {
-      if (from_front_q) { issue(c.fi, stage_front(c.fi), true); c.fi++; }
-      else { issue(c.bi, stage_back(c, c.bi), false); c.bi--; }
+  LineReg<T, KV> Lr, Rr;
+  bool hasL = false, hasR = false, ok = true;
+  for (;;) {
+    if (!hasL && pair_has_unread(c)) {
+      if (!take(c.fnext, Lr)) { ok = false; break; }
+      c.fnext++;
+      hasL = true;
     }
-    // write back full lines of P (front) and S (back) into consumed lines
-    while (c.fw <= c.bw && ctl_consumed(c, c.fw)) {
-      const uint32_t slot = line_tab_slot(c, c.fw);
-      const uint32_t lw = sm.tab_len[slot];
-      if (ctl_p_count(c) < lw) break;
-      if (lane == 0) flush(sm.pring, sm.vpring, c.p_head, sm.tab_line[slot], lw);
-      c.p_head += lw;
-      c.fw++;
+    if (!hasR && pair_has_unread(c)) {
+      if (!take(c.bnext, Rr)) { ok = false; break; }
+      c.bnext--;
+      hasR = true;
     }
-    while (c.bw >= c.fw && ctl_consumed(c, c.bw)) {
-      const uint32_t slot = line_tab_slot(c, c.bw);
-      const uint32_t lw = sm.tab_len[slot];
-      if (ctl_s_count(c) < lw) break;
-      if (lane == 0) flush(sm.sring, sm.vsring, c.s_head, sm.tab_line[slot], lw);
-      c.s_head += lw;
-      c.bw--;
+    if (!(hasL && hasR)) break;
+
+    // swap the j-th successor of L with the j-th predecessor of R
+    uint32_t bl[VPL * V], br[VPL * V];
+    uint32_t SL = 0, PR = 0;
+#pragma unroll
+    for (uint32_t u = 0; u < VPL; u++) {
+#pragma unroll
+      for (uint32_t v = 0; v < V; v++) {
+        const uint32_t bit = u * V + v;
+        const bool ls = ((Lr.valid >> u) & 1u) && !((Lr.pred >> bit) & 1u);
+        const bool rp = ((Rr.pred >> bit) & 1u) != 0u;
+        bl[bit] = __ballot_sync(FULL, ls);
+        br[bit] = __ballot_sync(FULL, rp);
+        SL += __popc(bl[bit]);
+        PR += __popc(br[bit]);
+      }
     }
-    if (lane == 0) bulk_wait_read<kPendingFlushes>();
-    __syncwarp();  // ring space of completed write-backs reusable
+    const uint32_t m = min(SL, PR);
+    if (m > 0) {
+      uint32_t rl[VPL * V], rr[VPL * V];
+      uint32_t al = 0, ar = 0;
+#pragma unroll
+      for (uint32_t bit = 0; bit < VPL * V; bit++) {
+        rl[bit] = ((bl[bit] >> lane) & 1u) ? al + __popc(bl[bit] & lt) : 0xffffffffu;
+        rr[bit] = ((br[bit] >> lane) & 1u) ? ar + __popc(br[bit] & lt) : 0xffffffffu;
+        al += __popc(bl[bit]);
+        ar += __popc(br[bit]);
+        const uint32_t u = bit / V, v = bit % V;
+        if (rl[bit] < m) {
+          sm.xbuf[0][rl[bit]] = Lr.x[u][v];
+          if constexpr (KV) sm.vxbuf[0][rl[bit]] = Lr.y[u][v];
+        }
+        if (rr[bit] < m) {
+          sm.xbuf[1][rr[bit]] = Rr.x[u][v];
+          if constexpr (KV) sm.vxbuf[1][rr[bit]] = Rr.y[u][v];
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (uint32_t bit = 0; bit < VPL * V; bit++) {
+        const uint32_t u = bit / V, v = bit % V;
+        if (rl[bit] < m) {
+          Lr.x[u][v] = sm.xbuf[1][rl[bit]];
+          if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][rl[bit]];
+          Lr.pred |= 1u << bit;
+        }
+        if (rr[bit] < m) {
+          Rr.x[u][v] = sm.xbuf[0][rr[bit]];
+          if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][rr[bit]];
+          Rr.pred &= ~(1u << bit);
+        }
+      }
+      __syncwarp();  // the buffer is free for the next swap
+    }
+    if (SL <= PR) { store_line(Lr); hasL = false; }
+    if (PR <= SL) { store_line(Rr); hasR = false; }
   }
 
   if (!ok) {
     // drain this warp's loads still in flight with bounded waits; the array
     // is left in an unspecified state and the status word says why
     if (lane == 0) {
-      for (int64_t l = c.lo_c; l <= c.hi_c; l++) {
+      atomicOr(status, kStatTimeout);
+      for (int64_t l = c.fnext; l <= c.bnext; l++) {
         if (l >= c.fi && l <= c.bi) continue;  // never issued
-        const uint32_t s2 = ctl_stage_of(c, l);
+        const uint32_t s2 = pair_stage_of(c, l);
         mbar_wait_bounded(&sm.bar[s2], (phase >> s2) & 1u);
       }
-      bulk_wait_all<0>();
     }
     __syncwarp();
     return false;
   }
 
-  // the last unwritten lines fw..bw take the rest of P, then the rest of S
-  const uint64_t pc = ctl_p_count(c), sc = ctl_s_count(c), rem = pc + sc;
-  for (uint64_t q = lane; q < rem; q += 32) {
-    const bool isp = q < pc;
-    const uint64_t r = isp ? ((c.p_head + q) & MASK) : ((c.s_head + (q - pc)) & MASK);
-    const int64_t m = c.fw + (int64_t)(q / G.b);
-    const uint64_t off = q % G.b;
-    const uint64_t gw = sm.tab_line[line_tab_slot(c, m)];
-    base[gw * G.b + off] = isp ? sm.pring[r] : sm.sring[r];
-    if constexpr (KV) vbase[gw * G.b + off] = isp ? sm.vpring[r] : sm.vsring[r];
+  // the one line left in hand: predecessors first, then successors
+  if (hasL || hasR) {
+    LineReg<T, KV>& F = hasL ? Lr : Rr;
+    uint32_t bp[VPL * V];
+    uint32_t P = 0;
+#pragma unroll
+    for (uint32_t bit = 0; bit < VPL * V; bit++) {
+      bp[bit] = __ballot_sync(FULL, (F.pred >> bit) & 1u);
+      P += __popc(bp[bit]);
+    }
+    uint32_t ap = 0, as = 0;
+    T* dst = base + (uint64_t)F.gl * G.b;
+    uint64_t* vdst = KV ? vbase + (uint64_t)F.gl * G.b : nullptr;
+#pragma unroll
+    for (uint32_t bit = 0; bit < VPL * V; bit++) {
+      const uint32_t u = bit / V, v = bit % V;
+      const uint32_t bs = __ballot_sync(FULL, ((F.valid >> u) & 1u) && !((F.pred >> bit) & 1u));
+      if ((bp[bit] >> lane) & 1u) {
+        const uint32_t pos = ap + __popc(bp[bit] & lt);
+        dst[pos] = F.x[u][v];
+        if constexpr (KV) vdst[pos] = F.y[u][v];
+      } else if ((bs >> lane) & 1u) {
+        const uint32_t pos = P + as + __popc(bs & lt);
+        dst[pos] = F.x[u][v];
+        if constexpr (KV) vdst[pos] = F.y[u][v];
+      }
+      ap += __popc(bp[bit]);
+      as += __popc(bs);
+    }
   }
-  k = c.k;
-  if (lane == 0) bulk_wait_read<0>();
-  __syncwarp();  // rings and table free for the next group
+  __syncwarp();
   return true;
 }
 

@@ -51,7 +51,8 @@ def group_of_positions(n, b, g, X):
     (1 << 16, 64, 16, 0), (1 << 16, 64, 16, 1), (100000, 32, 37, 0),
     (1 << 20, 64, 304, 0), ((1 << 20) + 4096 + 2, 64, 100, 0), (4096, 8, 3, 0),
     (2 * 1000, 2, 7, 0), (5000, 64, 3, 0), (30000, 16, 1, 0), (1 << 20, 64, 3000, 0),
-    ((1 << 22) + 18, 32, 2000, 0), (1 << 21, 64, 1, 0), (1 << 22, 64, 2432, 1)])
+    ((1 << 22) + 18, 32, 2000, 0), (1 << 21, 64, 1, 0), (1 << 22, 64, 2432, 1),
+    ((1 << 22) + 6, 128, 777, 0), (1 << 21, 128, 5000, 0)])
 def test_step_parity(ctx, n, b, g, strided):
     """One Partial Partition Step: v_min, v_max and the count equal the
     oracle's for the same X; every group is a predecessors-first permutation
@@ -105,7 +106,7 @@ def test_step_rejects_bad_args(ctx):
         lp.lp_smoothed_step(ctx, dev, P50, 3, 4)  # 24-byte line
     assert e.value.status == lp.LP_ERR_INVALID_ARG
     with pytest.raises(lp.LPError) as e:
-        lp.lp_smoothed_step(ctx, dev, P50, 128, 4)  # 1024-byte line: above the limit
+        lp.lp_smoothed_step(ctx, dev, P50, 256, 4)  # 2048-byte line: above the limit
     assert e.value.status == lp.LP_ERR_INVALID_ARG
 
 

@@ -1,12 +1,12 @@
-"""CPU emulation of the CTA-wide streaming group partition's control logic.
+"""CPU emulation of the per-warp line-pair partition's control logic.
 
-tests/csrc/emulate_stream.cpp runs the kernel's control decisions (from
-csrc/lp_plan.h, the header the kernel uses) with plain copies and asserts the
-hazards the GPU version must avoid: a line loaded twice or written before it
-was read, a stage refilled before it was consumed, a wrong mbarrier parity,
-ring appends over bytes a pending bulk store still reads, and an unpartitioned
-or non-permuted result.  Adversarial patterns (all / none / 1% / 99%
-predecessors, alternating, sorted, reverse) are included.
+tests/csrc/emulate_stream.cpp runs the kernel's control decisions (PairCtl and
+the stage map of csrc/lp_plan.h, the header the kernel uses) with plain copies
+and asserts the hazards the GPU version must avoid: a line loaded twice or
+written before it was taken, a stage refilled before it was taken or into the
+wrong slot, a wrong mbarrier parity, and an unpartitioned or non-permuted
+group.  Adversarial patterns (all / none / 1% / 99% predecessors,
+alternating, sorted, reverse) are included.
 """
 import os
 import subprocess
