@@ -148,6 +148,35 @@ lp_status lp_smoothed_step_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t
                                int strided, cudaStream_t stream, uint64_t *vmin,
                                uint64_t *vmax, uint64_t *count);
 
+/* ------------------------------------------------- allocation-free variant
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory where they need a partition -- code
+ * running inside another allocator's callback, latency-bound loops that must
+ * not pay cudaMalloc's implicit device synchronisation, processes whose
+ * device memory is entirely held by a framework's caching pool.  Such callers
+ * cannot create an lp_ctx, which allocates its scratch.
+ *
+ * lp_partition_u64_noalloc runs the same kernels as lp_partition_u64_async
+ * (LP_SMOOTHED or LP_STRIDED) on the current device and writes the split t to
+ * the device word *d_split when the stream gets there; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (the
+ * per-level descriptors and a status word, a few hundred bytes, independent
+ * of n) lives in one file-scope __device__ array of LP_NOALLOC_SCRATCH_BYTES
+ * bytes, which every GPU that loads this library keeps until the process
+ * exits.  The first call on a device resolves that array's device address
+ * and the launch grid (cudaGetSymbolAddress, occupancy queries); make that
+ * first call before capturing the stream into a CUDA graph.  All calls on a
+ * device share the one array: calls whose work overlaps on the GPU (other
+ * streams, or graphs launched concurrently) race on it and must be
+ * serialised by the caller.  Each call re-initialises the scratch it reads.
+ * Device-side status (a timed-out wait) is not reported; argument errors are
+ * LP_ERR_INVALID_ARG, a scratch need above the array's size (never the case
+ * for this partition) too, and CUDA failures LP_ERR_CUDA. */
+#define LP_NOALLOC_SCRATCH_BYTES 4096
+lp_status lp_partition_u64_noalloc(uint64_t *keys, uint64_t n, uint64_t pivot,
+                                   lp_variant variant, uint64_t seed, cudaStream_t stream,
+                                   uint64_t *d_split);
+
 /* ------------------------------------------------------- synthetic inputs
  * Fill d_keys[0..n) with outputs 0..n-1 of SplitMix64 started at `seed`
  * (Steele, Lea, Flood 2014); the u32 form keeps the low 32 bits.  These are

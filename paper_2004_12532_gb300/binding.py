@@ -53,6 +53,7 @@ _SIGS = {
                                   _pu64, _pu64, _pu64]),
     "lp_smoothed_step_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _u64, _u64, _i, _p,
                                   _pu64, _pu64, _pu64]),
+    "lp_partition_u64_noalloc": (_i, [_p, _u64, _u64, _i, _u64, _p, _p]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -208,6 +209,17 @@ def lp_partition_kv_u64_async(ctx, keys, vals, pivot, d_split, variant=LP_SMOOTH
     s, _ = _dev_ptr(d_split, 64)
     return ctx.check(lib().lp_partition_kv_u64_async(ctx.h, p, q, n, int(pivot), int(variant),
                                                      int(seed), _stream(stream), s))
+
+
+def lp_partition_u64_noalloc(keys, pivot, d_split, variant=LP_SMOOTHED, seed=0, stream=None):
+    """Allocation-free partition (no lp_ctx): t is written to d_split on the device.
+    For callers that cannot allocate device memory; see libpartition.h."""
+    p, n = _dev_ptr(keys, 64)
+    s, _ = _dev_ptr(d_split, 64)
+    st = lib().lp_partition_u64_noalloc(p, n, int(pivot), int(variant), int(seed),
+                                        _stream(stream), s)
+    if st != LP_OK:
+        raise LPError(st, "lp_partition_u64_noalloc")
 
 
 def lp_smoothed_step(ctx, keys, pivot, b, g, seed=0, level=0, strided=False, stream=None):
