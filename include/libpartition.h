@@ -89,11 +89,15 @@ lp_status lp_ctx_set_timing(lp_ctx *ctx, int enable);
 /* Level structure of the last Smoothed / Strided partition call on ctx (the
  * recursion of Sec. 4 on [v_min, v_max)): for level L < LP_MAX_LEVELS,
  * ranges[4L..4L+3] = {lo, hi, b, g} of the range that level partitioned
- * (all zero for a level that had nothing left to do), and, when timing was
- * enabled for that call, ms[L] = the level kernel's duration in milliseconds
- * (ms may be NULL).  Synchronises the last call's stream.  *levels receives
- * LP_MAX_LEVELS. */
+ * (all zero for a level that had nothing left to do; g == 0 marks the on-chip
+ * base case), and ms[L] = the level's duration in milliseconds from device
+ * timestamps (ms may be NULL).  Synchronises the last call's stream.
+ * *levels receives LP_MAX_LEVELS. */
 lp_status lp_ctx_level_stats(lp_ctx *ctx, uint64_t *ranges, float *ms, int *levels);
+/* Duration in milliseconds, from CUDA events on the call's stream, of the
+ * partition kernel of the last call on ctx (timing must have been enabled for
+ * that call).  Synchronises on the end event. */
+lp_status lp_ctx_kernel_ms(lp_ctx *ctx, float *ms);
 
 /* ---------------------------------------------------------------- partition
  * Partition keys[0..n) by [x <= pivot] (Sec. 2).  `variant` selects the
@@ -160,18 +164,19 @@ lp_status lp_smoothed_step_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t
  * (LP_SMOOTHED or LP_STRIDED) on the current device and writes the split t to
  * the device word *d_split when the stream gets there; it calls no
  * cudaMalloc, cudaFree or other allocating routine.  Its scratch (the
- * per-level descriptors and a status word, a few hundred bytes, independent
- * of n) lives in one file-scope __device__ array of LP_NOALLOC_SCRATCH_BYTES
- * bytes, which every GPU that loads this library keeps until the process
- * exits.  The first call on a device resolves that array's device address
+ * per-level descriptors, a status word, a grid barrier and one word per CTA
+ * of the launch: about 2 KB on a 152-SM GPU, independent of n) lives in one
+ * file-scope __device__ array of LP_NOALLOC_SCRATCH_BYTES bytes, which every
+ * GPU that loads this library keeps until the process exits.  The first call on a device resolves that array's device address
  * and the launch grid (cudaGetSymbolAddress, occupancy queries); make that
  * first call before capturing the stream into a CUDA graph.  All calls on a
  * device share the one array: calls whose work overlaps on the GPU (other
  * streams, or graphs launched concurrently) race on it and must be
  * serialised by the caller.  Each call re-initialises the scratch it reads.
  * Device-side status (a timed-out wait) is not reported; argument errors are
- * LP_ERR_INVALID_ARG, a scratch need above the array's size (never the case
- * for this partition) too, and CUDA failures LP_ERR_CUDA. */
+ * LP_ERR_INVALID_ARG, and so is a device whose launch grid would need more
+ * scratch than the array holds (more than about 700 CTAs); CUDA failures are
+ * LP_ERR_CUDA. */
 #define LP_NOALLOC_SCRATCH_BYTES 4096
 lp_status lp_partition_u64_noalloc(uint64_t *keys, uint64_t n, uint64_t pivot,
                                    lp_variant variant, uint64_t seed, cudaStream_t stream,

@@ -43,6 +43,7 @@ _SIGS = {
     "lp_ctx_grid": (_u32, [_p]),
     "lp_ctx_set_timing": (_i, [_p, _i]),
     "lp_ctx_level_stats": (_i, [_p, _pu64, C.POINTER(C.c_float), C.POINTER(_i)]),
+    "lp_ctx_kernel_ms": (_i, [_p, C.POINTER(C.c_float)]),
     "lp_partition_u64": (_i, [_p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
     "lp_partition_u32": (_i, [_p, _p, _u64, _u32, _i, _u64, _p, _pu64]),
     "lp_partition_kv_u64": (_i, [_p, _p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
@@ -146,6 +147,12 @@ class Ctx:
 
     def set_timing(self, on=True):
         self.check(lib().lp_ctx_set_timing(self.h, 1 if on else 0))
+
+    def kernel_ms(self):
+        """Event-timed duration of the last timed call's partition kernel (ms)."""
+        v = C.c_float()
+        self.check(lib().lp_ctx_kernel_ms(self.h, C.byref(v)))
+        return float(v.value)
 
     def level_stats(self):
         """[(lo, hi, b, g, ms)] for each level of the last partition call."""

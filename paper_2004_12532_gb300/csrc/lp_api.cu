@@ -25,7 +25,7 @@ struct lp_ctx {
   bool timing = false;
   bool events_made = false;
   bool last_timed = false;
-  cudaEvent_t ev[lp::kMaxLevels + 1];
+  cudaEvent_t ev[2];             // around the partition kernel of a timed call
   cudaStream_t last_stream = nullptr;
 };
 
@@ -178,16 +178,15 @@ lp_status lp_ctx_create(lp_ctx** out, int device) {
     delete c;
     return LP_ERR_CUDA;
   }
-  const size_t desc_bytes = lp::level_desc_bytes() * lp::kMaxLevels;
-  c->scratch_bytes = desc_bytes + 256;
+  uint32_t gmax = c->grid_u64;
+  if (c->grid_u32 > gmax) gmax = c->grid_u32;
+  if (c->grid_kv > gmax) gmax = c->grid_kv;
+  c->scratch_bytes = lp::task_scratch_bytes(gmax);
   e = cudaMalloc(&c->d_scratch, c->scratch_bytes);
   if (e != cudaSuccess) { delete c; return LP_ERR_OOM; }
   e = cudaMallocHost(reinterpret_cast<void**>(&c->h_pinned), 64);
   if (e != cudaSuccess) { cudaFree(c->d_scratch); delete c; return LP_ERR_OOM; }
-  unsigned char* base = static_cast<unsigned char*>(c->d_scratch);
-  c->task.desc = reinterpret_cast<lp::LevelDesc*>(base);
-  c->task.status = reinterpret_cast<uint32_t*>(base + desc_bytes);
-  c->task.split = reinterpret_cast<uint64_t*>(base + desc_bytes + 64);
+  c->task = lp::carve_scratch(c->d_scratch, gmax);
   c->aux_bytes = c->scratch_bytes;
   *out = c;
   return LP_OK;
@@ -197,7 +196,7 @@ lp_status lp_ctx_destroy(lp_ctx* c) {
   if (!c) return LP_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   if (c->events_made)
-    for (int i = 0; i <= lp::kMaxLevels; i++) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < 2; i++) cudaEventDestroy(c->ev[i]);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   delete c;
@@ -214,7 +213,7 @@ lp_status lp_ctx_set_timing(lp_ctx* c, int enable) {
   if (enable && !c->events_made) {
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    for (int i = 0; i <= lp::kMaxLevels; i++) {
+    for (int i = 0; i < 2; i++) {
       e = cudaEventCreate(&c->ev[i]);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
     }
@@ -231,24 +230,37 @@ lp_status lp_ctx_level_stats(lp_ctx* c, uint64_t* ranges, float* ms, int* levels
   e = cudaStreamSynchronize(c->last_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
   const size_t db = lp::level_desc_bytes();
+  uint64_t w[lp::kMaxLevels][8];
+  e = cudaMemcpy(w, c->task.desc, db * lp::kMaxLevels, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read levels");
+  uint64_t t_end = 0;
+  e = cudaMemcpy(&t_end, c->task.t_end, 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read end time");
   for (int L = 0; L < lp::kMaxLevels; L++) {
-    uint64_t w[8];
-    e = cudaMemcpy(w, reinterpret_cast<unsigned char*>(c->task.desc) + L * db, sizeof(w),
-                   cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "read level");
-    ranges[4 * L + 0] = w[3];  // lo
-    ranges[4 * L + 1] = w[4];  // hi
-    ranges[4 * L + 2] = w[5];  // b
-    ranges[4 * L + 3] = w[6];  // g
+    ranges[4 * L + 0] = w[L][3];  // lo
+    ranges[4 * L + 1] = w[L][4];  // hi
+    ranges[4 * L + 2] = w[L][5];  // b
+    ranges[4 * L + 3] = w[L][6];  // g
     if (ms) {
-      ms[L] = 0.f;
-      if (c->last_timed) {
-        e = cudaEventElapsedTime(&ms[L], c->ev[L], c->ev[L + 1]);
-        if (e != cudaSuccess) return cuda_fail(c, e, "event elapsed");
-      }
+      // device timestamps: a level ends when the next one starts
+      const uint64_t t0 = w[L][7];
+      uint64_t t1 = (L + 1 < lp::kMaxLevels && w[L + 1][7]) ? w[L + 1][7] : t_end;
+      ms[L] = (t0 && t1 > t0) ? (float)((double)(t1 - t0) * 1e-6) : 0.f;
     }
   }
   *levels = lp::kMaxLevels;
+  return LP_OK;
+}
+
+lp_status lp_ctx_kernel_ms(lp_ctx* c, float* ms) {
+  if (!c || !ms) return LP_ERR_INVALID_ARG;
+  if (!c->last_timed) return fail(c, LP_ERR_INVALID_ARG, "the last call was not timed");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  e = cudaEventSynchronize(c->ev[1]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "event synchronize");
+  e = cudaEventElapsedTime(ms, c->ev[0], c->ev[1]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "event elapsed");
   return LP_OK;
 }
 

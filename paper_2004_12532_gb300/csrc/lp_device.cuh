@@ -34,6 +34,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
                : "memory");
 }
 
+// Ends an mbarrier's life so its shared memory may be reused for data.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -105,6 +110,37 @@ __device__ __forceinline__ void bulk_wait_read() {
 template <int N>
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
+// counts arrivals, bar[1] is the generation; both start at zero.  The last
+// CTA to arrive resets the count and advances the generation; the others wait
+// for the generation to change, for at most kWaitLimitNs.  Returns false (in
+// every thread of the CTA) if this CTA gave up waiting.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks,
+                                             unsigned int* flag_smem) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int ok = 1u;
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1u) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      while (*gen == g0) {
+        if (global_timer_ns() - t0 > kWaitLimitNs) { ok = 0u; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *flag_smem = ok;
+  }
+  __syncthreads();
+  return *flag_smem != 0u;
 }
 
 }  // namespace lp

@@ -1,15 +1,18 @@
 // lp_kernels.cu -- kernels of the Recursive Smoothed Striding partition
 // (Sec. 4 of arXiv 2004.12532) and their host launchers.
 //
-//   desc_init_kernel     resets the per-level descriptors and the status word
-//   level_kernel         one Partial Partition Step over the range the previous
-//                        level left open ([v_min, v_max) of Sec. 4), with the
-//                        parameter rule of lp_plan.h; a range small enough runs
-//                        as one group, i.e. the paper's base case
-//   finalize_kernel      places the (< 16-byte) unaligned head and tail keys
-//                        and writes the split t
-//   small_kernel         whole partition of a short array in one CTA
-//   fill kernels         seeded synthetic inputs (SplitMix64), harness only
+//   desc_init_kernel   resets the level descriptors, status and grid barrier
+//   partition_kernel   the whole recursion in one cooperative launch: level 0
+//                      on the caller's range, then each level on the range
+//                      [v_min, v_max) the previous one left open (Sec. 4,
+//                      "Recurse on A[v_min] .. A[v_max - 1]"), a grid barrier
+//                      between levels; once the open range fits in the CTAs'
+//                      shared memory, the base case partitions it on chip
+//   level_kernel       one Partial Partition Step with explicit parameters
+//                      (the lp_smoothed_step entry point)
+//   finalize_kernel    places the (< 16-byte) unaligned head and tail keys and
+//                      writes the split t
+//   fill kernels       seeded synthetic inputs (SplitMix64), harness only
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,79 +23,249 @@ namespace lp {
 
 size_t level_desc_bytes() { return sizeof(LevelDesc); }
 
-__global__ void desc_init_kernel(LevelDesc* d, int count, uint32_t* status) {
-  int t = threadIdx.x;
-  if (t < count) {
-    d[t].vmin = ~0ull;
-    d[t].vmax = 0ull;
-    d[t].count = 0ull;
-    d[t].lo = d[t].hi = d[t].b = d[t].g = d[t].pad = 0ull;
-  }
-  if (t == 0) *status = 0u;
+// ------------------------------------------------------------ scratch layout
+size_t task_scratch_bytes(uint32_t grid) {
+  return sizeof(LevelDesc) * kMaxLevels + 64 /* status */ + 64 /* barrier, t_end */ +
+         ((size_t)grid * 4 + 63) / 64 * 64 /* counts */;
 }
 
-// Range of a level: the caller's range at level 0, else the previous level's
-// [v_min, v_max).  Extended outward to 16-byte boundaries of the body: keys
-// added on the left are already predecessors in final position and keys added
-// on the right successors, so partitioning the wider range is equivalent.
-__device__ __forceinline__ bool level_range(const LevelArgs& a, const LevelDesc* in,
-                                            uint32_t A, uint64_t& lo, uint64_t& hi) {
-  if (in) {
-    lo = in->vmin;
-    hi = in->vmax;
-    if (lo >= hi) return false;
-  } else {
-    lo = a.lo;
-    hi = a.hi;
-    if (lo >= hi) return false;
+TaskScratch carve_scratch(void* base, uint32_t grid) {
+  (void)grid;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  TaskScratch S;
+  S.desc = reinterpret_cast<LevelDesc*>(p);
+  p += sizeof(LevelDesc) * kMaxLevels;
+  S.status = reinterpret_cast<uint32_t*>(p);
+  S.split = reinterpret_cast<uint64_t*>(p + 8);
+  p += 64;
+  S.bar = reinterpret_cast<uint32_t*>(p);
+  S.t_end = reinterpret_cast<unsigned long long*>(p + 8);
+  p += 64;
+  S.counts = reinterpret_cast<uint32_t*>(p);
+  return S;
+}
+
+__global__ void desc_init_kernel(TaskScratch S) {
+  const int t = threadIdx.x;
+  if (t < kMaxLevels) {
+    LevelDesc& d = S.desc[t];
+    d.vmin = ~0ull;
+    d.vmax = 0ull;
+    d.count = 0ull;
+    d.lo = d.hi = d.b = d.g = d.t_start = 0ull;
   }
-  lo = a.body_lo + ((lo - a.body_lo) / A) * A;
-  uint64_t h2 = a.body_lo + ((hi - a.body_lo + A - 1) / A) * A;
-  hi = h2 < a.body_hi ? h2 : a.body_hi;
-  return lo < hi;
+  if (t == 0) {
+    *S.status = 0u;
+    S.bar[0] = 0u;
+    S.bar[1] = 0u;
+    *S.t_end = 0ull;
+  }
+}
+
+// Extends [lo, hi) outward to 16-byte boundaries of the body [body_lo,
+// body_hi): keys added on the left are predecessors already in final place and
+// keys added on the right successors, so partitioning the wider range is
+// equivalent.
+__device__ __forceinline__ void align_range(uint64_t body_lo, uint64_t body_hi, uint32_t A,
+                                            uint64_t& lo, uint64_t& hi) {
+  lo = body_lo + ((lo - body_lo) / A) * A;
+  const uint64_t h2 = body_lo + ((hi - body_lo + A - 1) / A) * A;
+  hi = h2 < body_hi ? h2 : body_hi;
 }
 
 template <typename T, bool KV>
+struct Coop {
+  // keys one CTA holds in the on-chip base case (a multiple of the 16-byte
+  // alignment unit), and the shared memory it uses
+  static constexpr size_t SmemBytes = level_smem_bytes<T, KV>();
+  static constexpr uint32_t Keys =
+      (uint32_t)((SmemBytes - 256) / (sizeof(T) + (KV ? 8 : 0))) / Tr<T, KV>::A * Tr<T, KV>::A;
+};
+
+// The base case on chip: the range base[0..n) is split into gridDim.x blocks
+// of B keys; every CTA stages its block in shared memory and counts its
+// predecessors; after a grid barrier each CTA knows the predecessors of the
+// blocks before it and writes its predecessors, then its successors, to their
+// final places (stable).  Every key is read once and written once.  All threads
+// of all CTAs call this.  Returns the predecessor count of the range, or
+// ~0 if this CTA gave up at the grid barrier.
+template <typename T, bool KV>
+__device__ uint64_t coop_finish(T* __restrict__ base, uint64_t* __restrict__ vbase, uint64_t n,
+                                T pivot, const TaskScratch& S, unsigned char* smem,
+                                unsigned int* flag) {
+  constexpr uint32_t NT = Tr<T, KV>::Threads, A = Tr<T, KV>::A;
+  uint32_t* wsum = reinterpret_cast<uint32_t*>(smem);  // 2 * NT/32 words
+  T* sk = reinterpret_cast<T*>(smem + 128);
+  uint64_t* sv = reinterpret_cast<uint64_t*>(smem + 128 + (size_t)Coop<T, KV>::Keys * sizeof(T));
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  uint64_t B = (n + gridDim.x - 1) / gridDim.x;
+  B = (B + A - 1) / A * A;
+  const uint64_t s0 = min((uint64_t)blockIdx.x * B, n), s1 = min(s0 + B, n);
+  const uint32_t m = (uint32_t)(s1 - s0);
+  for (uint32_t q = tid; q < m; q += NT) {
+    sk[q] = base[s0 + q];
+    if constexpr (KV) sv[q] = vbase[s0 + q];
+  }
+  __syncthreads();
+  const uint32_t per = (m + NT - 1) / NT;
+  const uint32_t q0 = min(m, tid * per), q1 = min(m, q0 + per);
+  uint32_t cnt = 0;
+  for (uint32_t q = q0; q < q1; q++) cnt += sk[q] <= pivot;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (uint32_t o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t wb = 0, tot = 0;
+  for (uint32_t w = 0; w < NT / 32; w++) {
+    wb += w < warp ? wsum[w] : 0u;
+    tot += wsum[w];
+  }
+  if (tid == 0) S.counts[blockIdx.x] = tot;
+  if (!grid_barrier(S.bar, gridDim.x, flag)) return ~0ull;
+  // predecessors before this block, and in the whole range
+  uint32_t before = 0, all = 0;
+  for (uint32_t c = tid; c < gridDim.x; c += NT) {
+    const uint32_t v = __ldcg(&S.counts[c]);
+    all += v;
+    if (c < blockIdx.x) before += v;
+  }
+  before = __reduce_add_sync(0xffffffffu, before);
+  all = __reduce_add_sync(0xffffffffu, all);
+  if (lane == 0) { wsum[NT / 32 + warp] = before; wsum[2 * (NT / 32) + warp] = all; }
+  __syncthreads();
+  uint64_t bsum = 0, asum = 0;
+  for (uint32_t w = 0; w < NT / 32; w++) {
+    bsum += wsum[NT / 32 + w];
+    asum += wsum[2 * (NT / 32) + w];
+  }
+  const uint32_t pre = wb + incl - cnt;  // predecessors before this thread's slice
+  uint64_t pp = bsum + pre;
+  uint64_t sp = asum + (s0 - bsum) + (q0 - pre);
+  for (uint32_t q = q0; q < q1; q++) {
+    const T x = sk[q];
+    const uint64_t d = x <= pivot ? pp++ : sp++;
+    base[d] = x;
+    if constexpr (KV) vbase[d] = sv[q];
+  }
+  return asum;
+}
+
+struct PartArgs {
+  uint64_t body_lo, body_hi;  // 16-byte aligned body of the array
+  uint64_t pivot, seed;
+  int strided;                // level 0 with X == 0 (the Strided Algorithm)
+};
+
+// The whole recursion in one cooperative launch; see the file comment.
+template <typename T, bool KV>
+__global__ void __launch_bounds__(Tr<T, KV>::Threads) partition_kernel(T* keys, uint64_t* vals,
+                                                                       PartArgs a,
+                                                                       TaskScratch S) {
+  using R = Tr<T, KV>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ unsigned int bar_flag;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  WarpSmem<T, KV>& ws = reinterpret_cast<WarpSmem<T, KV>*>(smem_raw)[warp];
+  if (lane == 0) {
+    for (uint32_t s = 0; s < kStages; s++) mbar_init(&ws.bar[s], 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  const uint64_t total_warps = (uint64_t)gridDim.x * R::Warps;
+  const uint64_t coop_cap = (uint64_t)gridDim.x * Coop<T, KV>::Keys;
+  const T pivot = (T)a.pivot;
+
+  for (int L = 0; L < kMaxLevels; L++) {
+    uint64_t lo, hi;
+    if (L == 0) {
+      lo = a.body_lo;
+      hi = a.body_hi;
+    } else {
+      lo = __ldcg(&S.desc[L - 1].vmin);
+      hi = __ldcg(&S.desc[L - 1].vmax);
+    }
+    if (lo >= hi) break;
+    align_range(a.body_lo, a.body_hi, R::A, lo, hi);
+    const uint64_t n = hi - lo;
+    if (leader) {
+      S.desc[L].lo = lo;
+      S.desc[L].hi = hi;
+      S.desc[L].t_start = global_timer_ns();
+    }
+    T* base = keys + lo;
+    uint64_t* vbase = KV ? vals + lo : nullptr;
+
+    if (n <= coop_cap) {  // the paper's base case, on chip
+      if (lane == 0)  // the finish reuses the stages' shared memory
+        for (uint32_t s2 = 0; s2 < kStages; s2++) mbar_inval(&ws.bar[s2]);
+      __syncthreads();
+      const uint64_t t = coop_finish<T, KV>(base, vbase, n, pivot, S, smem_raw, &bar_flag);
+      if (t == ~0ull) {
+        if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout);
+      } else if (leader) {
+        S.desc[L].vmin = lo + t;
+        S.desc[L].vmax = lo + t;
+        S.desc[L].count = t;
+        S.desc[L].b = 0;
+        S.desc[L].g = 0;
+      }
+      break;
+    }
+
+    // a Partial Partition Step (parameter rule of lp_plan.h); the last level,
+    // should a range still be open, is one group
+    const StepParams P = choose_params(n, R::K, total_warps, R::LineBytes);
+    const uint64_t b = P.b;
+    const uint64_t g = (L == kMaxLevels - 1) ? 1 : P.g;
+    if (leader) { S.desc[L].b = b; S.desc[L].g = g; }
+    const StepGeom G = make_geom(n, b, g, level_seed(a.seed, (uint64_t)L),
+                                 (a.strided && L == 0) ? 1 : 0);
+    for (uint64_t i = (uint64_t)blockIdx.x * R::Warps + warp; i < G.g; i += total_warps) {
+      const int32_t nl = (int32_t)group_num_lines(G, i);
+      uint64_t k = 0;
+      if (!warp_pair_group<T, KV>(base, vbase, G, (uint32_t)i, nl, pivot, ws, phase, k,
+                                  S.status))
+        break;  // the status is set; the barrier below still runs
+      if (nl > 0 && lane == 0) {
+        const unsigned long long v = lo + group_split_pos(G, i, (uint64_t)nl, k);
+        atomicMin(&S.desc[L].vmin, v);
+        atomicMax(&S.desc[L].vmax, v);
+        atomicAdd(&S.desc[L].count, (unsigned long long)k);
+      }
+    }
+    if (!grid_barrier(S.bar, gridDim.x, &bar_flag)) {
+      if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout);
+      break;
+    }
+    // stop on an error raised anywhere in this level; one thread reads the
+    // status so that the whole CTA takes the same branch
+    if (threadIdx.x == 0) bar_flag = __ldcg(S.status) == 0u ? 1u : 0u;
+    __syncthreads();
+    if (!bar_flag) break;
+  }
+  if (leader) *S.t_end = global_timer_ns();
+}
+
+// One Partial Partition Step with explicit parameters on [a.lo, a.hi).
+template <typename T, bool KV>
 __global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint64_t* vals,
-                                                                   LevelArgs a,
-                                                                   const LevelDesc* in,
-                                                                   LevelDesc* out,
+                                                                   LevelArgs a, LevelDesc* out,
                                                                    uint32_t* status) {
   using R = Tr<T, KV>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-
-  uint64_t lo, hi;
-  if (!level_range(a, in, R::A, lo, hi)) return;
-  const uint64_t n = hi - lo;
+  const uint64_t lo = a.lo, n = a.hi - a.lo;
   const uint64_t total_warps = (uint64_t)gridDim.x * R::Warps;
-
-  uint64_t b, g;
-  if (a.fixed_b) {
-    b = a.fixed_b;
-    g = a.fixed_g;
-  } else {
-    const StepParams P = choose_params(n, R::K, total_warps, R::LineBytes, R::FinishKeys);
-    b = P.b;
-    g = P.g;
-    if (a.force_finish && g != 0) g = 1;  // last level: one group takes the rest
-  }
+  const StepGeom G = make_geom(n, a.fixed_b, a.fixed_g, level_seed(a.seed, a.level), a.strided);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    out->lo = lo; out->hi = hi; out->b = b; out->g = g;
+    out->lo = lo; out->hi = a.hi; out->b = a.fixed_b; out->g = a.fixed_g;
   }
-  if (g == 0) {
-    // the paper's base case: one CTA partitions the range in shared memory
-    if (blockIdx.x != 0) return;
-    const uint32_t cnt = cta_partition_smem<T, KV>(keys + lo, KV ? vals + lo : nullptr,
-                                                   (uint32_t)n, (T)a.pivot, smem_raw);
-    if (threadIdx.x == 0) {
-      out->vmin = lo + cnt;
-      out->vmax = lo + cnt;
-      out->count = cnt;
-    }
-    return;
-  }
-
-  const StepGeom G = make_geom(n, b, g, level_seed(a.seed, a.level), a.strided);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint64_t gw = (uint64_t)blockIdx.x * R::Warps + warp;
   if (gw >= G.g) return;  // warps are independent: no CTA barrier below
@@ -103,15 +276,15 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint
     fence_proxy_async_smem();
   }
   __syncwarp();
-
   uint32_t phase = 0;
   T* base = keys + lo;
   uint64_t* vbase = KV ? vals + lo : nullptr;
   const T pivot = (T)a.pivot;
   for (uint64_t i = gw; i < G.g; i += total_warps) {
-    const int64_t nl = (int64_t)group_num_lines(G, i);
+    const int32_t nl = (int32_t)group_num_lines(G, i);
     uint64_t k = 0;
-    if (!warp_pair_group<T, KV>(base, vbase, G, i, nl, pivot, ws, phase, k, status)) break;
+    if (!warp_pair_group<T, KV>(base, vbase, G, (uint32_t)i, nl, pivot, ws, phase, k, status))
+      break;
     if (nl > 0 && lane == 0) {
       const unsigned long long v = lo + group_split_pos(G, i, (uint64_t)nl, k);
       atomicMin(&out->vmin, v);
@@ -127,11 +300,9 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint
 // final split t; there are at most a dozen, and one thread swaps them.
 template <typename T, bool KV>
 __global__ void finalize_kernel(T* keys, uint64_t* vals, uint64_t n, uint64_t h,
-                                uint64_t body_end, T pivot, const LevelDesc* d0,
-                                const LevelDesc* dlast, uint32_t* status, uint64_t* split) {
+                                uint64_t body_end, T pivot, TaskScratch S) {
   if (threadIdx.x != 0) return;
-  if (dlast->vmin < dlast->vmax) atomicOr(status, kStatUnfinished);
-  const uint64_t cb = d0->count;
+  const uint64_t cb = S.desc[0].count;
   const uint64_t m = h + cb;
   uint64_t hp = 0, tp = 0;
   for (uint64_t p = 0; p < h; p++) hp += keys[p] <= pivot;
@@ -151,7 +322,7 @@ __global__ void finalize_kernel(T* keys, uint64_t* vals, uint64_t n, uint64_t h,
   for (uint64_t p = r0; p < r1; p++) visit(p);
   for (uint64_t p = body_end; p < n; p++) visit(p);
   if (ns != np || ns >= 32) {
-    atomicOr(status, kStatRing);
+    atomicOr(S.status, kStatRing);
   } else {
     for (int q = 0; q < ns; q++) {
       T x = keys[bad_s[q]];
@@ -164,14 +335,15 @@ __global__ void finalize_kernel(T* keys, uint64_t* vals, uint64_t n, uint64_t h,
       }
     }
   }
-  *split = t;
+  *S.split = t;
 }
 
+// Whole partition of an array of n <= small_limit keys in one CTA (any
+// alignment), for arrays too short for a 16-byte aligned body.
 uint64_t small_limit(uint32_t key_bytes, bool kv) {
   return kFinishBytes / (key_bytes + (kv ? 8u : 0u));
 }
 
-// Whole partition of an array of n <= small_limit keys in one CTA.
 template <typename T, bool KV>
 __global__ void __launch_bounds__(Tr<T, KV>::Threads) small_kernel(T* keys, uint64_t* vals,
                                                                    uint32_t n, T pivot,
@@ -190,18 +362,25 @@ template <typename T, bool KV>
 cudaError_t streaming_grid(int device, uint32_t* grid) {
   cudaError_t e;
   const size_t smem = stream_smem_bytes<T, KV>();
+  e = cudaFuncSetAttribute(partition_kernel<T, KV>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(level_kernel<T, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(small_kernel<T, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
-  int sms = 0, per = 0;
+  int sms = 0, per = 0, per2 = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, level_kernel<T, KV>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, partition_kernel<T, KV>,
                                                     Tr<T, KV>::Threads, smem);
   if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, level_kernel<T, KV>,
+                                                    Tr<T, KV>::Threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per2 < per) per = per2;
   if (per < 1) per = 1;
   *grid = (uint32_t)(sms * per);
   return cudaSuccess;
@@ -212,45 +391,39 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
                             int strided, const TaskScratch& S, LaunchCfg& cfg) {
   using R = Tr<T, KV>;
   cudaStream_t st = cfg.stream;
+  const size_t smem = stream_smem_bytes<T, KV>();
+  desc_init_kernel<<<1, 32, 0, st>>>(S);
+  cfg.launches++;
   if (n <= small_limit(R::K, KV)) {
-    const size_t smem = stream_smem_bytes<T, KV>();
-    if (cfg.level_events)
-      for (int L = 0; L <= kMaxLevels; L++) cudaEventRecord(cfg.level_events[L], st);
+    if (cfg.events) cudaEventRecord(cfg.events[0], st);
     small_kernel<T, KV><<<1, R::Threads, smem, st>>>(keys, vals, (uint32_t)n, pivot, S.split);
     cfg.launches++;
-    desc_init_kernel<<<1, 32, 0, st>>>(S.desc, kMaxLevels, S.status);
-    cfg.launches++;
+    if (cfg.events) cudaEventRecord(cfg.events[1], st);
     return cudaGetLastError();
   }
   const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
   const uint64_t h = ((16 - (addr & 15)) & 15) / R::K;
   const uint64_t body_end = h + ((n - h) / R::A) * R::A;
-  const size_t smem = stream_smem_bytes<T, KV>();
-
-  desc_init_kernel<<<1, 32, 0, st>>>(S.desc, kMaxLevels, S.status);
+  PartArgs a;
+  a.body_lo = h;
+  a.body_hi = body_end;
+  a.pivot = (uint64_t)pivot;
+  a.seed = seed;
+  a.strided = strided;
+  // a range the CTAs can hold on chip needs only as many CTAs as it fills
+  uint64_t grid = cfg.grid;
+  const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
+  if (need < grid) grid = need ? need : 1;
+  TaskScratch Sv = S;
+  void* args[] = {&keys, &vals, &a, &Sv};
+  if (cfg.events) cudaEventRecord(cfg.events[0], st);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)partition_kernel<T, KV>,
+                                              dim3((unsigned)grid), dim3(R::Threads), args, smem,
+                                              st);
   cfg.launches++;
-  for (int L = 0; L < kMaxLevels; L++) {
-    LevelArgs a;
-    a.lo = h;
-    a.hi = body_end;
-    a.body_lo = h;
-    a.body_hi = body_end;
-    a.pivot = (uint64_t)pivot;
-    a.seed = seed;
-    a.level = (uint64_t)L;
-    a.fixed_b = 0;
-    a.fixed_g = 0;
-    a.strided = (strided && L == 0) ? 1 : 0;
-    a.force_finish = (L == kMaxLevels - 1) ? 1 : 0;
-    const LevelDesc* in = L ? S.desc + (L - 1) : nullptr;
-    if (cfg.level_events) cudaEventRecord(cfg.level_events[L], st);
-    level_kernel<T, KV><<<cfg.grid, R::Threads, smem, st>>>(keys, vals, a, in, S.desc + L,
-                                                            S.status);
-    cfg.launches++;
-  }
-  if (cfg.level_events) cudaEventRecord(cfg.level_events[kMaxLevels], st);
-  finalize_kernel<T, KV><<<1, 32, 0, st>>>(keys, vals, n, h, body_end, pivot, S.desc,
-                                           S.desc + (kMaxLevels - 1), S.status, S.split);
+  if (cfg.events) cudaEventRecord(cfg.events[1], st);
+  if (e != cudaSuccess) return e;
+  finalize_kernel<T, KV><<<1, 32, 0, st>>>(keys, vals, n, h, body_end, pivot, S);
   cfg.launches++;
   return cudaGetLastError();
 }
@@ -259,7 +432,7 @@ template <typename T>
 cudaError_t launch_step(T* keys, uint64_t n, T pivot, uint64_t b, uint64_t g, uint64_t seed,
                         uint64_t level, int strided, const TaskScratch& S, LaunchCfg& cfg) {
   cudaStream_t st = cfg.stream;
-  desc_init_kernel<<<1, 32, 0, st>>>(S.desc, kMaxLevels, S.status);
+  desc_init_kernel<<<1, 32, 0, st>>>(S);
   cfg.launches++;
   LevelArgs a;
   a.lo = 0;
@@ -274,7 +447,7 @@ cudaError_t launch_step(T* keys, uint64_t n, T pivot, uint64_t b, uint64_t g, ui
   a.strided = strided;
   a.force_finish = 0;
   level_kernel<T, false><<<cfg.grid, Tr<T, false>::Threads, stream_smem_bytes<T, false>(), st>>>(
-      keys, nullptr, a, nullptr, S.desc, S.status);
+      keys, nullptr, a, S.desc, S.status);
   cfg.launches++;
   return cudaGetLastError();
 }

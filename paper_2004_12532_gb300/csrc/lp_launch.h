@@ -15,13 +15,21 @@ struct TaskScratch {
   LevelDesc* desc;     // kMaxLevels records
   uint32_t* status;    // device status bits
   uint64_t* split;     // where the split t is written
+  uint32_t* bar;       // grid barrier: arrival count, generation
+  uint32_t* counts;    // one word per CTA of the partition kernel
+  unsigned long long* t_end;  // device time at the end of the last level
 };
 
+// Bytes of TaskScratch for a partition kernel of `grid` CTAs, laid out by
+// carve_scratch from a 256-byte aligned base.
+size_t task_scratch_bytes(uint32_t grid);
+TaskScratch carve_scratch(void* base, uint32_t grid);
+
 struct LaunchCfg {
-  uint32_t grid;       // CTAs of the streaming kernels
+  uint32_t grid;       // CTAs of the streaming kernels (co-resident)
   cudaStream_t stream;
   uint64_t launches;   // incremented per kernel launch
-  cudaEvent_t* level_events;  // optional, kMaxLevels + 1 events around the levels
+  cudaEvent_t* events; // optional: two events around the partition kernel
 };
 
 // Keys-only (KV = false, vals == nullptr) and key+payload (KV = true, T = uint64_t).

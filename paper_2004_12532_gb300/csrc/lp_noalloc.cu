@@ -6,10 +6,11 @@
 // loops where the implicit device synchronisation of cudaMalloc is not
 // acceptable, and processes whose device memory is entirely reserved by a
 // framework's caching pool.  They cannot create an lp_ctx (which allocates its
-// scratch), so this entry point keeps the few hundred bytes of scratch the
-// partition needs -- the per-level descriptors and a status word -- in a
-// file-scope __device__ array instead.  It launches the same kernels as
-// lp_partition_u64_async and calls no allocating routine.
+// scratch), so this entry point keeps the scratch the partition needs -- the
+// per-level descriptors, a status word, the grid barrier and one count per CTA
+// of the launch, about 2 KB on a 152-SM GPU -- in a file-scope __device__
+// array instead.  It launches the same kernels as lp_partition_u64_async and
+// calls no allocating routine.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,9 +35,6 @@ struct DeviceSetup {
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
 
-// Bytes of scratch one partition needs: the level descriptors, then the
-// status word.  Independent of n.
-size_t scratch_needed() { return lp::level_desc_bytes() * lp::kMaxLevels + 64; }
 
 // Once per device, with that device current: resolve the array's device
 // address and the launch grid.  No allocation.
@@ -65,7 +63,6 @@ extern "C" lp_status lp_partition_u64_noalloc(uint64_t* keys, uint64_t n, uint64
   if (n > 0 && !keys) return LP_ERR_INVALID_ARG;
   if (variant != LP_SMOOTHED && variant != LP_STRIDED) return LP_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(keys) & 7) != 0) return LP_ERR_INVALID_ARG;
-  if (scratch_needed() > kScratchBytes) return LP_ERR_INVALID_ARG;  // scratch too small
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LP_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return LP_ERR_INVALID_ARG;
@@ -73,10 +70,10 @@ extern "C" lp_status lp_partition_u64_noalloc(uint64_t* keys, uint64_t n, uint64
   DeviceSetup* d = nullptr;
   const lp_status st = setup_device(dev, &d);
   if (st != LP_OK) return st;
-  unsigned char* base = static_cast<unsigned char*>(d->scratch);
-  lp::TaskScratch S;
-  S.desc = reinterpret_cast<lp::LevelDesc*>(base);
-  S.status = reinterpret_cast<uint32_t*>(base + lp::level_desc_bytes() * lp::kMaxLevels);
+  // the scratch grows with the launch grid (one word per CTA): refuse a
+  // device whose grid needs more than the array holds
+  if (lp::task_scratch_bytes(d->grid) > kScratchBytes) return LP_ERR_INVALID_ARG;
+  lp::TaskScratch S = lp::carve_scratch(d->scratch, d->grid);
   S.split = d_split;
   lp::LaunchCfg cfg{d->grid, stream, 0, nullptr};
   const cudaError_t e = lp::launch_smoothed<uint64_t, false>(

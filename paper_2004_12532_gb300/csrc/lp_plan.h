@@ -25,10 +25,10 @@ namespace lp {
 // lines in flight per side in shared memory.
 constexpr uint32_t kLineBytesMax = 1024;   // largest line in key bytes (2 vectors per lane)
 constexpr uint32_t kLineBytesMin = 128;    // smallest line used by the parameter rule
-constexpr uint32_t kQ = 4;                 // loads in flight per side (front / back)
+constexpr uint32_t kQ = 4;                 // loads in flight per side (a power of two)
 constexpr uint32_t kStages = 2 * kQ;       // input stages per warp
 constexpr uint32_t kFinishBytes = 64 * 1024;  // ranges up to this size: one CTA in smem
-constexpr uint32_t kMinChunks = 64;        // s at least this large when g > 1
+constexpr uint32_t kMinChunks = 8;         // lines per group, at least (when g > 1)
 
 // ------------------------------------------------------------ random source
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output k of the generator
@@ -117,29 +117,20 @@ LP_HD uint64_t group_split_pos(const StepGeom& G, uint64_t i, uint64_t nl, uint6
 }
 
 // ------------------------------------------------------------ parameter rule
-// Chooses the line size b and the group count g of one step on n keys of
-// key_bytes each, for `groups_max` concurrent group workers (warps) and lines
-// of at most line_bytes_max bytes.  Large ranges get the largest line that
-// still leaves at least kMinChunks chunks with one group per worker; smaller
-// ranges get shorter lines, then fewer groups.  g == 0 means: at most
-// finish_keys keys, which one CTA partitions in shared memory (the paper's
-// base case).
+// Line size b and group count g of one step on n keys of key_bytes each, with
+// `workers` warps each taking one group: the largest line, one group per warp,
+// but at least kMinChunks chunks (lines per group).  Each level then shrinks
+// the open range by roughly s / 3 at least; a range the CTAs can hold on chip
+// is finished there instead (the paper's base case).
 struct StepParams { uint64_t b, g; };
 
-LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t groups_max,
-                               uint32_t line_bytes_max, uint64_t finish_keys) {
+LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t workers,
+                               uint32_t line_bytes) {
   StepParams P;
-  P.b = line_bytes_max / key_bytes;
-  P.g = 0;
-  if (n <= finish_keys) return P;
-  for (uint32_t lb = line_bytes_max; lb >= kLineBytesMin; lb >>= 1) {
-    const uint64_t b = lb / key_bytes;
-    const uint64_t g = n / (b * kMinChunks);
-    P.b = b;
-    P.g = g;
-    if (g >= groups_max) { P.g = groups_max; return P; }
-  }
-  if (P.g < 2) P.g = 2;
+  P.b = line_bytes / key_bytes;
+  P.g = n / (P.b * kMinChunks);
+  if (P.g > workers) P.g = workers;
+  if (P.g < 1) P.g = 1;
   return P;
 }
 
@@ -154,21 +145,21 @@ LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t groups_m
 // Lines are loaded ahead from both ends, kQ per side; `fi` / `bi` are the next
 // lines to load from the front / back, [fnext, bnext] the lines not yet taken.
 struct PairCtl {
-  int64_t nl;          // lines in the group
-  int64_t fi, bi;      // next line to load from the front / the back
-  int64_t fnext, bnext;  // lines not yet taken: [fnext, bnext]
+  int32_t nl;            // lines in the group
+  int32_t fi, bi;        // next line to load from the front / the back
+  int32_t fnext, bnext;  // lines not yet taken: [fnext, bnext]
 };
 
-LP_HD void pair_init(PairCtl& c, int64_t nl) {
+LP_HD void pair_init(PairCtl& c, int32_t nl) {
   c.nl = nl; c.fi = 0; c.bi = nl - 1; c.fnext = 0; c.bnext = nl - 1;
 }
 LP_HD bool pair_can_issue(const PairCtl& c) { return c.fi <= c.bi; }
-LP_HD uint32_t pair_stage_front(int64_t line) { return (uint32_t)(line % kQ); }
-LP_HD uint32_t pair_stage_back(const PairCtl& c, int64_t line) {
-  return kQ + (uint32_t)((c.nl - 1 - line) % kQ);
+LP_HD uint32_t pair_stage_front(int32_t line) { return (uint32_t)line & (kQ - 1); }
+LP_HD uint32_t pair_stage_back(const PairCtl& c, int32_t line) {
+  return kQ + ((uint32_t)(c.nl - 1 - line) & (kQ - 1));
 }
 // Stage holding an issued line: lines below fi came from the front queue.
-LP_HD uint32_t pair_stage_of(const PairCtl& c, int64_t line) {
+LP_HD uint32_t pair_stage_of(const PairCtl& c, int32_t line) {
   return line < c.fi ? pair_stage_front(line) : pair_stage_back(c, line);
 }
 LP_HD bool pair_has_unread(const PairCtl& c) { return c.fnext <= c.bnext; }

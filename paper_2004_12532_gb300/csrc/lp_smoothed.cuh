@@ -38,8 +38,8 @@ struct LevelDesc {
   unsigned long long vmax;   // max over groups of v_i
   unsigned long long count;  // sum over groups of k_i
   unsigned long long lo, hi; // the (aligned) range this level worked on
-  unsigned long long b, g;   // parameters used (g == 0: finished in one CTA)
-  unsigned long long pad;
+  unsigned long long b, g;   // parameters used (g == 0: the on-chip base case)
+  unsigned long long t_start;  // device time (ns) when the level started
 };
 
 // Arguments of one level launch.
@@ -122,104 +122,108 @@ struct LineReg {
 // control is warp-uniform, lane 0 issues the bulk copies.  `phase` holds one
 // parity bit per stage and persists across the warp's groups.  Returns false
 // if a bounded wait gave up (after draining the warp's copies in flight);
-// k receives the group's predecessor count.
+// k receives the group's predecessor count.  Lines are indexed in 32 bits
+// (the range has fewer than 2^31 lines; the host and parameter rule keep it so).
 template <typename T, bool KV>
 __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vbase,
-                                const StepGeom& G, uint64_t i, int64_t nl, T pivot,
+                                const StepGeom& G, uint32_t i, int32_t nl, T pivot,
                                 WarpSmem<T, KV>& sm, uint32_t& phase, uint64_t& k,
                                 uint32_t* status) {
   using R = Tr<T, KV>;
-  constexpr uint32_t V = R::V, VPL = R::VPL;
+  constexpr uint32_t V = R::V, VPL = R::VPL, NB = VPL * V;
   constexpr uint32_t FULL = 0xffffffffu;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
   k = 0;
   if (nl <= 0) return true;
 
+  // per-step constants in 32 bits
+  const uint32_t g32 = (uint32_t)G.g, b32 = (uint32_t)G.b;
+  const uint32_t last_line = (uint32_t)(G.L - 1);
+  const uint32_t last_len = (uint32_t)(G.n - (G.L - 1) * G.b);
+
   // X windows: lane l holds X[wf + l] (front) and X[wb - l] (back)
-  int64_t wf = -64, wb = -64;
-  uint64_t xf = 0, xb = 0;
-  auto x_front = [&](int64_t m) -> uint64_t {
-    if (G.strided) return 0;
-    if (m < wf || m >= wf + 32) {
-      wf = m;
-      const uint64_t j = (uint64_t)wf + lane;
-      xf = j < G.s ? range_of(sm_stream(G.sigma, j), G.g) : 0;
-    }
-    return __shfl_sync(FULL, xf, (int)(m - wf));
-  };
-  auto x_back = [&](int64_t m) -> uint64_t {
-    if (G.strided) return 0;
-    if (m > wb || m <= wb - 32) {
-      wb = m;
-      const int64_t j = wb - (int64_t)lane;
-      xb = j >= 0 ? range_of(sm_stream(G.sigma, (uint64_t)j), G.g) : 0;
-    }
-    return __shfl_sync(FULL, xb, (int)(wb - m));
-  };
+  int32_t wf = -64, wb = -64;
+  uint32_t xf = 0, xb = 0;
 
   PairCtl c;
   pair_init(c, nl);
 
-  auto issue = [&](int64_t line, uint32_t st, bool front) {
-    const uint64_t x = front ? x_front(line) : x_back(line);
-    uint64_t off = x + i;
-    if (off >= G.g) off -= G.g;
-    const uint64_t gl = (uint64_t)line * G.g + off;
-    const uint32_t len = (uint32_t)line_len(G, gl);
+  auto issue = [&](int32_t line, uint32_t st, bool front) {
+    uint32_t x = 0;
+    if (!G.strided) {
+      if (front) {
+        if (line < wf || line >= wf + 32) {
+          wf = line;
+          const uint64_t j = (uint64_t)(uint32_t)wf + lane;
+          xf = j < G.s ? (uint32_t)range_of(sm_stream(G.sigma, j), G.g) : 0u;
+        }
+        x = __shfl_sync(FULL, xf, line - wf);
+      } else {
+        if (line > wb || line <= wb - 32) {
+          wb = line;
+          const int32_t j = wb - (int32_t)lane;
+          xb = j >= 0 ? (uint32_t)range_of(sm_stream(G.sigma, (uint64_t)j), G.g) : 0u;
+        }
+        x = __shfl_sync(FULL, xb, wb - line);
+      }
+    }
+    uint32_t off = x + i;
+    if (off >= g32) off -= g32;
+    const uint32_t gl = (uint32_t)line * g32 + off;
     if (lane == 0) {
-      sm.st_line[st] = (uint32_t)gl;
+      const uint32_t len = gl == last_line ? last_len : b32;
+      sm.st_line[st] = gl;
       sm.st_len[st] = len;
       const uint32_t bytes = len * R::K;
       mbar_arrive_expect_tx(&sm.bar[st], KV ? 2u * bytes : bytes);
-      bulk_load(&sm.stage[st][0], base + gl * G.b, bytes, &sm.bar[st]);
-      if constexpr (KV) bulk_load(&sm.vstage[st][0], vbase + gl * G.b, bytes, &sm.bar[st]);
+      bulk_load(&sm.stage[st][0], base + (size_t)gl * b32, bytes, &sm.bar[st]);
+      if constexpr (KV) bulk_load(&sm.vstage[st][0], vbase + (size_t)gl * b32, bytes, &sm.bar[st]);
     }
   };
   // take an issued line into registers; refill its stage; false on timeout
-  auto take = [&](int64_t line, LineReg<T, KV>& Lr) -> bool {
+  auto take = [&](int32_t line, LineReg<T, KV>& Lr) -> bool {
     const uint32_t st = pair_stage_of(c, line);
-    const bool front_stage = st < kQ;
     const bool arrived = mbar_wait_bounded(&sm.bar[st], (phase >> st) & 1u);
     if (!__all_sync(FULL, arrived)) return false;
     phase ^= 1u << st;
     Lr.gl = sm.st_line[st];
     Lr.len = sm.st_len[st];
     const uint32_t nvec = Lr.len / V;
-    Lr.pred = 0;
-    Lr.valid = 0;
+    uint32_t pred = 0, valid = 0;
 #pragma unroll
     for (uint32_t u = 0; u < VPL; u++) {
       const uint32_t vec = u * 32u + lane;
       if (vec < nvec) {
-        Lr.valid |= 1u << u;
+        valid |= 1u << u;
         load_vec<T>(&sm.stage[st][vec * V], Lr.x[u]);
         if constexpr (KV) {
           const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&sm.vstage[st][vec * V]);
           Lr.y[u][0] = w.x; Lr.y[u][1] = w.y;
         }
 #pragma unroll
-        for (uint32_t v = 0; v < V; v++)
-          Lr.pred |= (Lr.x[u][v] <= pivot ? 1u : 0u) << (u * V + v);
+        for (uint32_t v = 0; v < V; v++) pred |= (Lr.x[u][v] <= pivot ? 1u : 0u) << (u * V + v);
       }
     }
-    k += (uint64_t)__reduce_add_sync(FULL, __popc(Lr.pred));
+    Lr.pred = pred;
+    Lr.valid = valid;
+    k += __reduce_add_sync(FULL, __popc(pred));
     __syncwarp();  // every lane has read the stage: it may be refilled
     if (pair_can_issue(c)) {
-      if (front_stage) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
+      if (st < kQ) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
       else { issue(c.bi, pair_stage_back(c, c.bi), false); c.bi--; }
     }
     return true;
   };
   auto store_line = [&](const LineReg<T, KV>& Lr) {
-    T* dst = base + (uint64_t)Lr.gl * G.b;
+    T* dst = base + (size_t)Lr.gl * b32;
 #pragma unroll
     for (uint32_t u = 0; u < VPL; u++) {
       if ((Lr.valid >> u) & 1u) {
         const uint32_t vec = u * 32u + lane;
         store_vec<T>(dst + vec * V, Lr.x[u]);
         if constexpr (KV) {
-          *reinterpret_cast<ulonglong2*>(vbase + (uint64_t)Lr.gl * G.b + vec * V) =
+          *reinterpret_cast<ulonglong2*>(vbase + (size_t)Lr.gl * b32 + vec * V) =
               make_ulonglong2(Lr.y[u][0], Lr.y[u][1]);
         }
       }
@@ -248,54 +252,54 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     if (!(hasL && hasR)) break;
 
     // swap the j-th successor of L with the j-th predecessor of R
-    uint32_t bl[VPL * V], br[VPL * V];
+    uint32_t lkeys = 0;  // bit j: key slot j of L exists
+#pragma unroll
+    for (uint32_t u = 0; u < VPL; u++)
+      if ((Lr.valid >> u) & 1u) lkeys |= ((1u << V) - 1u) << (u * V);
+    const uint32_t lsucc = ~Lr.pred & lkeys;
+    const uint32_t rpred = Rr.pred;
+    uint32_t bl[NB], br[NB];
     uint32_t SL = 0, PR = 0;
 #pragma unroll
-    for (uint32_t u = 0; u < VPL; u++) {
-#pragma unroll
-      for (uint32_t v = 0; v < V; v++) {
-        const uint32_t bit = u * V + v;
-        const bool ls = ((Lr.valid >> u) & 1u) && !((Lr.pred >> bit) & 1u);
-        const bool rp = ((Rr.pred >> bit) & 1u) != 0u;
-        bl[bit] = __ballot_sync(FULL, ls);
-        br[bit] = __ballot_sync(FULL, rp);
-        SL += __popc(bl[bit]);
-        PR += __popc(br[bit]);
-      }
+    for (uint32_t j = 0; j < NB; j++) {
+      bl[j] = __ballot_sync(FULL, (lsucc >> j) & 1u);
+      br[j] = __ballot_sync(FULL, (rpred >> j) & 1u);
+      SL += __popc(bl[j]);
+      PR += __popc(br[j]);
     }
     const uint32_t m = min(SL, PR);
     if (m > 0) {
-      uint32_t rl[VPL * V], rr[VPL * V];
       uint32_t al = 0, ar = 0;
+      uint32_t rl[NB], rr[NB];
 #pragma unroll
-      for (uint32_t bit = 0; bit < VPL * V; bit++) {
-        rl[bit] = ((bl[bit] >> lane) & 1u) ? al + __popc(bl[bit] & lt) : 0xffffffffu;
-        rr[bit] = ((br[bit] >> lane) & 1u) ? ar + __popc(br[bit] & lt) : 0xffffffffu;
-        al += __popc(bl[bit]);
-        ar += __popc(br[bit]);
-        const uint32_t u = bit / V, v = bit % V;
-        if (rl[bit] < m) {
-          sm.xbuf[0][rl[bit]] = Lr.x[u][v];
-          if constexpr (KV) sm.vxbuf[0][rl[bit]] = Lr.y[u][v];
+      for (uint32_t j = 0; j < NB; j++) {
+        const uint32_t u = j / V, v = j % V;
+        rl[j] = ((lsucc >> j) & 1u) ? al + __popc(bl[j] & lt) : 0xffffffffu;
+        rr[j] = ((rpred >> j) & 1u) ? ar + __popc(br[j] & lt) : 0xffffffffu;
+        al += __popc(bl[j]);
+        ar += __popc(br[j]);
+        if (rl[j] < m) {
+          sm.xbuf[0][rl[j]] = Lr.x[u][v];
+          if constexpr (KV) sm.vxbuf[0][rl[j]] = Lr.y[u][v];
         }
-        if (rr[bit] < m) {
-          sm.xbuf[1][rr[bit]] = Rr.x[u][v];
-          if constexpr (KV) sm.vxbuf[1][rr[bit]] = Rr.y[u][v];
+        if (rr[j] < m) {
+          sm.xbuf[1][rr[j]] = Rr.x[u][v];
+          if constexpr (KV) sm.vxbuf[1][rr[j]] = Rr.y[u][v];
         }
       }
       __syncwarp();
 #pragma unroll
-      for (uint32_t bit = 0; bit < VPL * V; bit++) {
-        const uint32_t u = bit / V, v = bit % V;
-        if (rl[bit] < m) {
-          Lr.x[u][v] = sm.xbuf[1][rl[bit]];
-          if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][rl[bit]];
-          Lr.pred |= 1u << bit;
+      for (uint32_t j = 0; j < NB; j++) {
+        const uint32_t u = j / V, v = j % V;
+        if (rl[j] < m) {
+          Lr.x[u][v] = sm.xbuf[1][rl[j]];
+          if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][rl[j]];
+          Lr.pred |= 1u << j;
         }
-        if (rr[bit] < m) {
-          Rr.x[u][v] = sm.xbuf[0][rr[bit]];
-          if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][rr[bit]];
-          Rr.pred &= ~(1u << bit);
+        if (rr[j] < m) {
+          Rr.x[u][v] = sm.xbuf[0][rr[j]];
+          if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][rr[j]];
+          Rr.pred &= ~(1u << j);
         }
       }
       __syncwarp();  // the buffer is free for the next swap
@@ -309,7 +313,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     // is left in an unspecified state and the status word says why
     if (lane == 0) {
       atomicOr(status, kStatTimeout);
-      for (int64_t l = c.fnext; l <= c.bnext; l++) {
+      for (int32_t l = c.fnext; l <= c.bnext; l++) {
         if (l >= c.fi && l <= c.bi) continue;  // never issued
         const uint32_t s2 = pair_stage_of(c, l);
         mbar_wait_bounded(&sm.bar[s2], (phase >> s2) & 1u);
@@ -322,22 +326,22 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
   // the one line left in hand: predecessors first, then successors
   if (hasL || hasR) {
     LineReg<T, KV>& F = hasL ? Lr : Rr;
-    uint32_t bp[VPL * V];
+    uint32_t bp[NB];
     uint32_t P = 0;
 #pragma unroll
-    for (uint32_t bit = 0; bit < VPL * V; bit++) {
-      bp[bit] = __ballot_sync(FULL, (F.pred >> bit) & 1u);
-      P += __popc(bp[bit]);
+    for (uint32_t j = 0; j < NB; j++) {
+      bp[j] = __ballot_sync(FULL, (F.pred >> j) & 1u);
+      P += __popc(bp[j]);
     }
     uint32_t ap = 0, as = 0;
-    T* dst = base + (uint64_t)F.gl * G.b;
-    uint64_t* vdst = KV ? vbase + (uint64_t)F.gl * G.b : nullptr;
+    T* dst = base + (size_t)F.gl * b32;
+    uint64_t* vdst = KV ? vbase + (size_t)F.gl * b32 : nullptr;
 #pragma unroll
-    for (uint32_t bit = 0; bit < VPL * V; bit++) {
-      const uint32_t u = bit / V, v = bit % V;
-      const uint32_t bs = __ballot_sync(FULL, ((F.valid >> u) & 1u) && !((F.pred >> bit) & 1u));
-      if ((bp[bit] >> lane) & 1u) {
-        const uint32_t pos = ap + __popc(bp[bit] & lt);
+    for (uint32_t j = 0; j < NB; j++) {
+      const uint32_t u = j / V, v = j % V;
+      const uint32_t bs = __ballot_sync(FULL, ((F.valid >> u) & 1u) && !((F.pred >> j) & 1u));
+      if ((bp[j] >> lane) & 1u) {
+        const uint32_t pos = ap + __popc(bp[j] & lt);
         dst[pos] = F.x[u][v];
         if constexpr (KV) vdst[pos] = F.y[u][v];
       } else if ((bs >> lane) & 1u) {
@@ -345,7 +349,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
         dst[pos] = F.x[u][v];
         if constexpr (KV) vdst[pos] = F.y[u][v];
       }
-      ap += __popc(bp[bit]);
+      ap += __popc(bp[j]);
       as += __popc(bs);
     }
   }
