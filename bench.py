@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--log2n", type=int, default=30)
+    ap.add_argument("--log2n", type=int, default=None,
+                    help="default 30 (u64), 31 (u32), 29 (kv)")
+    ap.add_argument("--dtype", choices=["u64", "u32", "kv"], default="u64")
+    ap.add_argument("--quantile", type=int, default=50, help="percent of keys <= pivot")
     ap.add_argument("--variant", choices=["smoothed", "strided"], default="smoothed")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
@@ -77,7 +80,7 @@ def kernel_hash():
 def profiled_traffic(n_keys):
     """dram read+write bytes per level-0 launch from the committed ncu summary,
     scaled to n_keys, if the summary was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "level_kernel_u64_ncu.txt")
+    path = os.path.join(ROOT, "profiles", "partition_kernel_u64_ncu.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -213,19 +216,38 @@ def run_ours(args):
     from paper_2004_12532_gb300 import binding as lp
 
     n = 1 << args.log2n
-    K = 8
-    pivot = inputs.quantile_pivot(1, 2)
+    dt = args.dtype
+    K = 4 if dt == "u32" else 8          # key bytes
+    E = 16 if dt == "kv" else K          # bytes moved per key (key + payload)
+    pivot = inputs.quantile_pivot(args.quantile, 100, 32 if dt == "u32" else 64)
     variant = lp.LP_SMOOTHED if args.variant == "smoothed" else lp.LP_STRIDED
-    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    keys = torch.empty(n, dtype=torch.int32 if dt == "u32" else torch.int64, device="cuda")
+    vals = torch.empty(n, dtype=torch.int64, device="cuda") if dt == "kv" else None
     d_split = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def fill(seed):
+        if dt == "u32":
+            lp.lp_fill_uniform_u32(keys, seed)
+        else:
+            lp.lp_fill_uniform_u64(keys, seed)
+        if vals is not None:
+            lp.lp_fill_iota_u64(vals)
+
+    def part(seed):
+        if dt == "u32":
+            lp.lp_partition_u32_async(ctx, keys, pivot, d_split, variant, seed=seed)
+        elif dt == "kv":
+            lp.lp_partition_kv_u64_async(ctx, keys, vals, pivot, d_split, variant, seed=seed)
+        else:
+            lp.lp_partition_u64_async(ctx, keys, pivot, d_split, variant, seed=seed)
     ctx = lp.Ctx(local)
     ctx.set_timing(True)
     stream = torch.cuda.current_stream()
     seed0 = args.seed + 7919 * rank
 
     for w in range(args.warmup):
-        lp.lp_fill_uniform_u64(keys, seed0 + 100000 + w)
-        lp.lp_partition_u64_async(ctx, keys, pivot, d_split, variant, seed=w)
+        fill(seed0 + 100000 + w)
+        part(w)
     torch.cuda.synchronize()
 
     def barrier():
@@ -242,9 +264,9 @@ def run_ours(args):
     wall0 = time.perf_counter()
     clocks.start()
     for k in range(args.steps):
-        lp.lp_fill_uniform_u64(keys, seed0 + k)
+        fill(seed0 + k)
         ev0.record(stream)
-        lp.lp_partition_u64_async(ctx, keys, pivot, d_split, variant, seed=k)
+        part(k)
         ev1.record(stream)
         ev1.synchronize()
         part_ms.append(ev0.elapsed_time(ev1))
@@ -268,31 +290,36 @@ def run_ours(args):
         x = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         ms_all = float(x.item())
-    value = ws * 3 * K * n / (ms_all / 1e3) / 1e9
+    value = ws * 3 * E * n / (ms_all / 1e3) / 1e9
 
     peak, peak_kind = measured_peaks()
     k_ms = sum(kern_ms) / len(kern_ms)
     k_keys = sum(traffic_keys) / len(traffic_keys)
-    k_bytes = 2 * K * k_keys  # one read and one write of every key of every level
+    k_bytes = 2 * E * k_keys  # one read and one write of every key of every level
     achieved = k_bytes / (k_ms / 1e3) / 1e9
-    traffic = profiled_traffic(k_keys)
+    traffic = profiled_traffic(k_keys) if dt == "u64" else None
     l0_ms = sum(lvl0_ms) / len(lvl0_ms)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "partition_kernel<uint64_t> (all levels, one cooperative launch)",
+                "kernel": "partition_kernel<%s> (all levels, one cooperative launch)" % (
+                    {"u64": "uint64_t", "u32": "uint32_t", "kv": "uint64_t, payload"}[dt]),
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": k_bytes,
                 "ms_per_launch": k_ms,
-                "level0_gbs_device_timestamps": 2 * K * (sum(lvl0_n) / len(lvl0_n)) /
+                "level0_gbs_device_timestamps": 2 * E * (sum(lvl0_n) / len(lvl0_n)) /
                 (l0_ms / 1e3) / 1e9 if l0_ms > 0 else None}
 
+    metric = METRIC if (dt == "u64" and args.log2n == 30) else \
+        "in-place partition GB/s (%s, n=2^%d)" % ({"u64": "uint64", "u32": "uint32",
+                                                   "kv": "uint64 key + uint64 payload"}[dt],
+                                                  args.log2n)
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if dt == "u32" else "u64",
         "data": "synthetic (SplitMix64 uniform keys, seeded)",
-        "config": {"workload": "partition u64 n=2^%d pivot=2^63-1 (50%%) %s" % (
-                       args.log2n, args.variant),
-                   "n": n, "pivot": pivot, "variant": args.variant,
+        "config": {"workload": "partition %s n=2^%d pivot at %d%% quantile, %s" % (
+                       dt, args.log2n, args.quantile, args.variant),
+                   "n": n, "pivot": pivot, "variant": args.variant, "dtype": dt,
                    "l2": "inputs larger than L2 (8 GiB), regenerated on device between steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": roofline,
@@ -307,9 +334,9 @@ def run_ours(args):
     if clk:
         result["clocks"] = clk
 
-    if not args.no_e2e:
+    if not args.no_e2e and dt == "u64":
         result["e2e"] = e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream)
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu and dt == "u64":
         gbs, ns, reps, med = cpu_oracle_gbs(min(args.log2n, 27), pivot, args.seed)
         result["cpu_baseline"] = {
             "value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -352,6 +379,8 @@ def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):
 
 def main():
     args = parse()
+    if args.log2n is None:
+        args.log2n = {"u64": 30, "u32": 31, "kv": 29}[args.dtype]
     if args.impl == "reference":
         run_reference(args)
     else:
