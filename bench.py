@@ -55,7 +55,8 @@ def parse():
                     help="default 30 (u64), 31 (u32), 29 (kv)")
     ap.add_argument("--dtype", choices=["u64", "u32", "kv"], default="u64")
     ap.add_argument("--quantile", type=int, default=50, help="percent of keys <= pivot")
-    ap.add_argument("--variant", choices=["smoothed", "strided"], default="smoothed")
+    ap.add_argument("--variant", choices=["smoothed", "strided", "lowspace", "hybrid"],
+                    default="smoothed")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -220,7 +221,8 @@ def run_ours(args):
     K = 4 if dt == "u32" else 8          # key bytes
     E = 16 if dt == "kv" else K          # bytes moved per key (key + payload)
     pivot = inputs.quantile_pivot(args.quantile, 100, 32 if dt == "u32" else 64)
-    variant = lp.LP_SMOOTHED if args.variant == "smoothed" else lp.LP_STRIDED
+    variant = {"smoothed": lp.LP_SMOOTHED, "strided": lp.LP_STRIDED,
+               "lowspace": lp.LP_LOWSPACE, "hybrid": lp.LP_HYBRID}[args.variant]
     keys = torch.empty(n, dtype=torch.int32 if dt == "u32" else torch.int64, device="cuda")
     vals = torch.empty(n, dtype=torch.int64, device="cuda") if dt == "kv" else None
     d_split = torch.zeros(1, dtype=torch.int64, device="cuda")

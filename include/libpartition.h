@@ -58,9 +58,12 @@ typedef enum {
 
 typedef enum {
   LP_SMOOTHED = 0, /* Recursive Smoothed Striding (Sec. 4) */
-  LP_STRIDED = 1,  /* Strided Algorithm: the step with X == 0, then cleanup */
+  LP_STRIDED = 1,  /* Strided Algorithm: the step with X == 0, then the open
+                      range [v_min, v_max) by LP_LOWSPACE (the paper's cleanup is
+                      serial) */
   LP_LOWSPACE = 2, /* Blocked-Prefix-Sum partition (Sec. 3), explicit prefix */
-  LP_HYBRID = 3    /* Hybrid Smoothed Striding: one step, residual by LOWSPACE */
+  LP_HYBRID = 3    /* Hybrid Smoothed Striding (Theorem 4.3): one step with
+                      random X, the open range by LP_LOWSPACE */
 } lp_variant;
 
 typedef struct lp_ctx lp_ctx;
@@ -127,6 +130,25 @@ lp_status lp_partition_u32_async(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32
 lp_status lp_partition_kv_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t *vals,
                                     uint64_t n, uint64_t pivot, lp_variant variant,
                                     uint64_t seed, cudaStream_t stream, uint64_t *d_split);
+
+/* ------------------------------------------ Blocked-Prefix-Sum partition
+ * The low-space partition of Sec. 3 with explicit block size: count the
+ * predecessors (swapping the roles on the reversed array when they are the
+ * majority), MakeSuccessorHeavy (Lemma 3.1), per-block predecessor counts and
+ * their prefix in floor(n/B) explicit 8-byte counters (as the paper's
+ * implementation stores them, Sec. 5), then Reorder (the reordering lemma)
+ * from the innermost prefix outward.  base_keys == 0 finishes the innermost
+ * prefix at the paper's size (at most 5B keys); a larger value finishes it on
+ * chip once it has at most base_keys keys (capped by what the device's shared
+ * memory holds).  LP_LOWSPACE in lp_partition_* is this call with B = 4096.
+ * Scratch: about 8n/B bytes plus 8 bytes per CTA, held by ctx.  *split_out
+ * (host) receives t; synchronises `stream`. */
+lp_status lp_lowspace_partition_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
+                                    uint64_t B, uint64_t base_keys, cudaStream_t stream,
+                                    uint64_t *split_out);
+lp_status lp_lowspace_partition_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t pivot,
+                                    uint64_t B, uint64_t base_keys, cudaStream_t stream,
+                                    uint64_t *split_out);
 
 /* ------------------------------------------------- one Partial Partition Step
  * Runs exactly one Partial Partition Step (Sec. 4, "Formal Algorithm

@@ -55,6 +55,8 @@ _SIGS = {
     "lp_smoothed_step_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _u64, _u64, _i, _p,
                                   _pu64, _pu64, _pu64]),
     "lp_partition_u64_noalloc": (_i, [_p, _u64, _u64, _i, _u64, _p, _p]),
+    "lp_lowspace_partition_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _p, _pu64]),
+    "lp_lowspace_partition_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _p, _pu64]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -227,6 +229,16 @@ def lp_partition_u64_noalloc(keys, pivot, d_split, variant=LP_SMOOTHED, seed=0, 
                                         _stream(stream), s)
     if st != LP_OK:
         raise LPError(st, "lp_partition_u64_noalloc")
+
+
+def lp_lowspace_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):
+    """Blocked-Prefix-Sum partition with block size B; returns the split t."""
+    bits = keys.element_size() * 8
+    p, n = _dev_ptr(keys, bits)
+    f = lib().lp_lowspace_partition_u64 if bits == 64 else lib().lp_lowspace_partition_u32
+    t = C.c_uint64()
+    ctx.check(f(ctx.h, p, n, int(pivot), int(B), int(base_keys), _stream(stream), C.byref(t)))
+    return int(t.value)
 
 
 def lp_smoothed_step(ctx, keys, pivot, b, g, seed=0, level=0, strided=False, stream=None):

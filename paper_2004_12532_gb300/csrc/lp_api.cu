@@ -27,6 +27,8 @@ struct lp_ctx {
   bool last_timed = false;
   cudaEvent_t ev[2];             // around the partition kernel of a timed call
   cudaStream_t last_stream = nullptr;
+  void* d_var = nullptr;         // per-call scratch of the low-space partition (grown)
+  size_t var_bytes = 0;
 };
 
 namespace {
@@ -68,6 +70,24 @@ lp_status read_back(lp_ctx* c, cudaStream_t stream, uint64_t* split_out) {
   return status_to_lp(c, st);
 }
 
+// Grows the context's per-call scratch to at least `bytes` (a stream-ordered
+// free of the old buffer is not needed: the stream is synchronised first).
+lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream) {
+  if (bytes <= c->var_bytes) return LP_OK;
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  if (c->d_var) cudaFree(c->d_var);
+  c->d_var = nullptr;
+  c->var_bytes = 0;
+  e = cudaMalloc(&c->d_var, bytes);
+  if (e != cudaSuccess) return fail(c, LP_ERR_OOM, "scratch allocation failed");
+  c->var_bytes = bytes;
+  c->aux_bytes = c->scratch_bytes + c->var_bytes;
+  return LP_OK;
+}
+
+constexpr uint64_t kLowspaceBlock = 4096;  // B of the low-space partition (Sec. 5)
+
 template <typename T, bool KV>
 lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot,
                          lp_variant variant, uint64_t seed, cudaStream_t stream,
@@ -75,8 +95,9 @@ lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot
   if (!c) return LP_ERR_INVALID_ARG;
   c->err.clear();
   c->last_launches = 0;
-  if (variant != LP_SMOOTHED && variant != LP_STRIDED)
-    return fail(c, LP_ERR_INVALID_ARG, "variant not available");
+  if (variant != LP_SMOOTHED && variant != LP_STRIDED && variant != LP_LOWSPACE &&
+      variant != LP_HYBRID)
+    return fail(c, LP_ERR_INVALID_ARG, "unknown variant");
   if (n > 0 && (!keys || (KV && !vals))) return fail(c, LP_ERR_INVALID_ARG, "null array");
   if (!aligned_to(keys, sizeof(T)) || (KV && !aligned_to(vals, 8)))
     return fail(c, LP_ERR_INVALID_ARG, "array not naturally aligned");
@@ -99,8 +120,39 @@ lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot
                     c->timing ? c->ev : nullptr};
   c->last_timed = c->timing;
   c->last_stream = stream;
-  e = lp::launch_smoothed<T, KV>(keys, vals, n, pivot, seed, variant == LP_STRIDED ? 1 : 0, S,
-                                 cfg);
+  const bool small = n <= lp::small_limit(sizeof(T), KV);
+  if (variant == LP_SMOOTHED || small) {
+    e = lp::launch_smoothed<T, KV>(keys, vals, n, pivot, seed, 0, S, cfg);
+  } else if (variant == LP_LOWSPACE) {
+    lp_status ls = ensure_var(c, lp::lowspace_scratch_bytes(n, kLowspaceBlock, cfg.grid), stream);
+    if (ls != LP_OK) return ls;
+    e = cudaSuccess;
+    // the status word and grid barrier start clean
+    e = cudaMemsetAsync(S.status, 0, 4, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.bar, 0, 8, stream);
+    if (cfg.events && e == cudaSuccess) e = cudaEventRecord(cfg.events[0], stream);
+    if (e == cudaSuccess)
+      e = lp::launch_lowspace<T, KV>(keys, vals, 0, n, n, nullptr, pivot, kLowspaceBlock, ~0ull,
+                                     c->d_var, S, S.split, cfg);
+    if (cfg.events && e == cudaSuccess) e = cudaEventRecord(cfg.events[1], stream);
+  } else {
+    // Strided (X == 0) or Hybrid (random X): one Partial Partition Step, then
+    // the open range [v_min, v_max) by the low-space partition
+    lp_status ls = ensure_var(c, lp::lowspace_scratch_bytes(n, kLowspaceBlock, cfg.grid), stream);
+    if (ls != LP_OK) return ls;
+    uint64_t h = 0, body_end = 0;
+    cudaEvent_t* evs = cfg.events;
+    cfg.events = nullptr;
+    if (evs) cudaEventRecord(evs[0], stream);
+    e = lp::launch_first_level<T, KV>(keys, vals, n, pivot, seed, variant == LP_STRIDED ? 1 : 0,
+                                      S, cfg, &h, &body_end);
+    if (e == cudaSuccess)
+      e = lp::launch_lowspace<T, KV>(keys, vals, 0, 0, n, S.desc, pivot, kLowspaceBlock, ~0ull,
+                                     c->d_var, S, nullptr, cfg);
+    if (evs && e == cudaSuccess) e = cudaEventRecord(evs[1], stream);
+    if (e == cudaSuccess) e = lp::launch_finalize<T, KV>(keys, vals, n, h, body_end, pivot, S, cfg);
+    cfg.events = evs;
+  }
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return cuda_fail(c, e, "launch");
   if (split_out) {
@@ -160,6 +212,35 @@ lp_status step_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t b, uint64_
   return status_to_lp(c, (uint32_t)c->h_pinned[3]);
 }
 
+template <typename T>
+lp_status lowspace_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t B, uint64_t base_keys,
+                        cudaStream_t stream, uint64_t* split_out) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->err.clear();
+  c->last_launches = 0;
+  if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
+  if (n > 0 && !keys) return fail(c, LP_ERR_INVALID_ARG, "null array");
+  if (B == 0) return fail(c, LP_ERR_INVALID_ARG, "block size must be positive");
+  if (!aligned_to(keys, sizeof(T))) return fail(c, LP_ERR_INVALID_ARG, "array not aligned");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  if (n == 0) { *split_out = 0; return LP_OK; }
+  lp::LaunchCfg cfg{sizeof(T) == 8 ? c->grid_u64 : c->grid_u32, stream, 0, nullptr};
+  c->last_timed = false;
+  c->last_stream = stream;
+  lp_status ls = ensure_var(c, lp::lowspace_scratch_bytes(n, B, cfg.grid), stream);
+  if (ls != LP_OK) return ls;
+  lp::TaskScratch S = c->task;
+  e = cudaMemsetAsync(S.status, 0, 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.bar, 0, 8, stream);
+  if (e == cudaSuccess)
+    e = lp::launch_lowspace<T, false>(keys, nullptr, 0, n, n, nullptr, pivot, B,
+                                      base_keys ? base_keys : 1, c->d_var, S, S.split, cfg);
+  c->last_launches = cfg.launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "launch");
+  return read_back(c, stream, split_out);
+}
+
 }  // namespace
 
 extern "C" {
@@ -198,6 +279,7 @@ lp_status lp_ctx_destroy(lp_ctx* c) {
   if (c->events_made)
     for (int i = 0; i < 2; i++) cudaEventDestroy(c->ev[i]);
   if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->d_var) cudaFree(c->d_var);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   delete c;
   return LP_OK;
@@ -317,6 +399,17 @@ lp_status lp_smoothed_step_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t p
                                uint64_t* count) {
   return step_impl<uint32_t>(c, keys, n, pivot, b, g, seed, level, strided, s, vmin, vmax,
                              count);
+}
+
+lp_status lp_lowspace_partition_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
+                                    uint64_t B, uint64_t base_keys, cudaStream_t s,
+                                    uint64_t* split_out) {
+  return lowspace_impl<uint64_t>(c, keys, n, pivot, B, base_keys, s, split_out);
+}
+lp_status lp_lowspace_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
+                                    uint64_t B, uint64_t base_keys, cudaStream_t s,
+                                    uint64_t* split_out) {
+  return lowspace_impl<uint32_t>(c, keys, n, pivot, B, base_keys, s, split_out);
 }
 
 lp_status lp_fill_uniform_u64(uint64_t* d, uint64_t n, uint64_t seed, cudaStream_t s) {

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lp_coop.cuh"
 #include "lp_launch.h"
 #include "lp_smoothed.cuh"
 
@@ -73,91 +74,11 @@ __device__ __forceinline__ void align_range(uint64_t body_lo, uint64_t body_hi, 
   hi = h2 < body_hi ? h2 : body_hi;
 }
 
-template <typename T, bool KV>
-struct Coop {
-  // keys one CTA holds in the on-chip base case (a multiple of the 16-byte
-  // alignment unit), and the shared memory it uses
-  static constexpr size_t SmemBytes = level_smem_bytes<T, KV>();
-  static constexpr uint32_t Keys =
-      (uint32_t)((SmemBytes - 256) / (sizeof(T) + (KV ? 8 : 0))) / Tr<T, KV>::A * Tr<T, KV>::A;
-};
-
-// The base case on chip: the range base[0..n) is split into gridDim.x blocks
-// of B keys; every CTA stages its block in shared memory and counts its
-// predecessors; after a grid barrier each CTA knows the predecessors of the
-// blocks before it and writes its predecessors, then its successors, to their
-// final places (stable).  Every key is read once and written once.  All threads
-// of all CTAs call this.  Returns the predecessor count of the range, or
-// ~0 if this CTA gave up at the grid barrier.
-template <typename T, bool KV>
-__device__ uint64_t coop_finish(T* __restrict__ base, uint64_t* __restrict__ vbase, uint64_t n,
-                                T pivot, const TaskScratch& S, unsigned char* smem,
-                                unsigned int* flag) {
-  constexpr uint32_t NT = Tr<T, KV>::Threads, A = Tr<T, KV>::A;
-  uint32_t* wsum = reinterpret_cast<uint32_t*>(smem);  // 2 * NT/32 words
-  T* sk = reinterpret_cast<T*>(smem + 128);
-  uint64_t* sv = reinterpret_cast<uint64_t*>(smem + 128 + (size_t)Coop<T, KV>::Keys * sizeof(T));
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  uint64_t B = (n + gridDim.x - 1) / gridDim.x;
-  B = (B + A - 1) / A * A;
-  const uint64_t s0 = min((uint64_t)blockIdx.x * B, n), s1 = min(s0 + B, n);
-  const uint32_t m = (uint32_t)(s1 - s0);
-  for (uint32_t q = tid; q < m; q += NT) {
-    sk[q] = base[s0 + q];
-    if constexpr (KV) sv[q] = vbase[s0 + q];
-  }
-  __syncthreads();
-  const uint32_t per = (m + NT - 1) / NT;
-  const uint32_t q0 = min(m, tid * per), q1 = min(m, q0 + per);
-  uint32_t cnt = 0;
-  for (uint32_t q = q0; q < q1; q++) cnt += sk[q] <= pivot;
-  uint32_t incl = cnt;
-#pragma unroll
-  for (uint32_t o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  uint32_t wb = 0, tot = 0;
-  for (uint32_t w = 0; w < NT / 32; w++) {
-    wb += w < warp ? wsum[w] : 0u;
-    tot += wsum[w];
-  }
-  if (tid == 0) S.counts[blockIdx.x] = tot;
-  if (!grid_barrier(S.bar, gridDim.x, flag)) return ~0ull;
-  // predecessors before this block, and in the whole range
-  uint32_t before = 0, all = 0;
-  for (uint32_t c = tid; c < gridDim.x; c += NT) {
-    const uint32_t v = __ldcg(&S.counts[c]);
-    all += v;
-    if (c < blockIdx.x) before += v;
-  }
-  before = __reduce_add_sync(0xffffffffu, before);
-  all = __reduce_add_sync(0xffffffffu, all);
-  if (lane == 0) { wsum[NT / 32 + warp] = before; wsum[2 * (NT / 32) + warp] = all; }
-  __syncthreads();
-  uint64_t bsum = 0, asum = 0;
-  for (uint32_t w = 0; w < NT / 32; w++) {
-    bsum += wsum[NT / 32 + w];
-    asum += wsum[2 * (NT / 32) + w];
-  }
-  const uint32_t pre = wb + incl - cnt;  // predecessors before this thread's slice
-  uint64_t pp = bsum + pre;
-  uint64_t sp = asum + (s0 - bsum) + (q0 - pre);
-  for (uint32_t q = q0; q < q1; q++) {
-    const T x = sk[q];
-    const uint64_t d = x <= pivot ? pp++ : sp++;
-    base[d] = x;
-    if constexpr (KV) vbase[d] = sv[q];
-  }
-  return asum;
-}
-
 struct PartArgs {
   uint64_t body_lo, body_hi;  // 16-byte aligned body of the array
   uint64_t pivot, seed;
   int strided;                // level 0 with X == 0 (the Strided Algorithm)
+  int max_levels;             // 1: level 0 only, the open range left for a cleanup
 };
 
 // The whole recursion in one cooperative launch; see the file comment.
@@ -182,7 +103,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) partition_kernel(T* keys, 
   const uint64_t coop_cap = (uint64_t)gridDim.x * Coop<T, KV>::Keys;
   const T pivot = (T)a.pivot;
 
-  for (int L = 0; L < kMaxLevels; L++) {
+  for (int L = 0; L < a.max_levels; L++) {
     uint64_t lo, hi;
     if (L == 0) {
       lo = a.body_lo;
@@ -410,6 +331,7 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
   a.pivot = (uint64_t)pivot;
   a.seed = seed;
   a.strided = strided;
+  a.max_levels = kMaxLevels;
   // a range the CTAs can hold on chip needs only as many CTAs as it fills
   uint64_t grid = cfg.grid;
   const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
@@ -424,6 +346,49 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
   if (cfg.events) cudaEventRecord(cfg.events[1], st);
   if (e != cudaSuccess) return e;
   finalize_kernel<T, KV><<<1, 32, 0, st>>>(keys, vals, n, h, body_end, pivot, S);
+  cfg.launches++;
+  return cudaGetLastError();
+}
+
+template <typename T, bool KV>
+cudaError_t launch_first_level(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64_t seed,
+                               int strided, const TaskScratch& S, LaunchCfg& cfg, uint64_t* hp,
+                               uint64_t* body_endp) {
+  using R = Tr<T, KV>;
+  cudaStream_t st = cfg.stream;
+  const size_t smem = stream_smem_bytes<T, KV>();
+  desc_init_kernel<<<1, 32, 0, st>>>(S);
+  cfg.launches++;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+  const uint64_t h = ((16 - (addr & 15)) & 15) / R::K;
+  const uint64_t body_end = h + ((n - h) / R::A) * R::A;
+  *hp = h;
+  *body_endp = body_end;
+  PartArgs a;
+  a.body_lo = h;
+  a.body_hi = body_end;
+  a.pivot = (uint64_t)pivot;
+  a.seed = seed;
+  a.strided = strided;
+  a.max_levels = 1;
+  uint64_t grid = cfg.grid;
+  const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
+  if (need < grid) grid = need ? need : 1;
+  TaskScratch Sv = S;
+  void* args[] = {&keys, &vals, &a, &Sv};
+  if (cfg.events) cudaEventRecord(cfg.events[0], st);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)partition_kernel<T, KV>,
+                                              dim3((unsigned)grid), dim3(R::Threads), args, smem,
+                                              st);
+  cfg.launches++;
+  if (cfg.events) cudaEventRecord(cfg.events[1], st);
+  return e;
+}
+
+template <typename T, bool KV>
+cudaError_t launch_finalize(T* keys, uint64_t* vals, uint64_t n, uint64_t h, uint64_t body_end,
+                            T pivot, const TaskScratch& S, LaunchCfg& cfg) {
+  finalize_kernel<T, KV><<<1, 32, 0, cfg.stream>>>(keys, vals, n, h, body_end, pivot, S);
   cfg.launches++;
   return cudaGetLastError();
 }
@@ -500,6 +465,16 @@ template cudaError_t launch_smoothed<uint32_t, false>(uint32_t*, uint64_t*, uint
 template cudaError_t launch_smoothed<uint64_t, true>(uint64_t*, uint64_t*, uint64_t, uint64_t,
                                                      uint64_t, int, const TaskScratch&,
                                                      LaunchCfg&);
+#define LP_INST_FIRST(T, KV)                                                                  \
+  template cudaError_t launch_first_level<T, KV>(T*, uint64_t*, uint64_t, T, uint64_t, int,       \
+                                                 const TaskScratch&, LaunchCfg&, uint64_t*,       \
+                                                 uint64_t*);                                      \
+  template cudaError_t launch_finalize<T, KV>(T*, uint64_t*, uint64_t, uint64_t, uint64_t, T,    \
+                                              const TaskScratch&, LaunchCfg&);
+LP_INST_FIRST(uint64_t, false)
+LP_INST_FIRST(uint32_t, false)
+LP_INST_FIRST(uint64_t, true)
+#undef LP_INST_FIRST
 template cudaError_t launch_step<uint64_t>(uint64_t*, uint64_t, uint64_t, uint64_t, uint64_t,
                                            uint64_t, uint64_t, int, const TaskScratch&,
                                            LaunchCfg&);

@@ -39,6 +39,27 @@ template <typename T, bool KV>
 cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64_t seed,
                             int strided, const TaskScratch& S, LaunchCfg& cfg);
 
+// Blocked-Prefix-Sum partition (lp_lowspace.cu) of keys[lo..hi), or of the
+// range [vmin, vmax) of *range_desc when it is set; the range has at most
+// n_cap keys and `var` holds lowspace_scratch_bytes(n_cap, B, grid) bytes.
+// split: where to write the predecessor count (may be null).
+size_t lowspace_scratch_bytes(uint64_t n, uint64_t B, uint32_t grid);
+template <typename T, bool KV>
+cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, uint64_t n_cap,
+                            const LevelDesc* range_desc, T pivot, uint64_t B, uint64_t base_keys,
+                            void* var, const TaskScratch& S, uint64_t* split, LaunchCfg& cfg);
+
+// Smoothed Striding level 0 only (the Strided Algorithm's partial step when
+// strided != 0), leaving [vmin, vmax) in S.desc[0] for a cleanup; then
+// finalize_smoothed places the unaligned head and tail and writes the split.
+template <typename T, bool KV>
+cudaError_t launch_first_level(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64_t seed,
+                               int strided, const TaskScratch& S, LaunchCfg& cfg, uint64_t* h,
+                               uint64_t* body_end);
+template <typename T, bool KV>
+cudaError_t launch_finalize(T* keys, uint64_t* vals, uint64_t n, uint64_t h, uint64_t body_end,
+                            T pivot, const TaskScratch& S, LaunchCfg& cfg);
+
 // One Partial Partition Step with explicit parameters over keys[0..n).
 template <typename T>
 cudaError_t launch_step(T* keys, uint64_t n, T pivot, uint64_t b, uint64_t g, uint64_t seed,

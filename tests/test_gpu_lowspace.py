@@ -1,0 +1,97 @@
+"""GPU parity of the Blocked-Prefix-Sum (low-space) partition and of the
+variants that clean up with it (Strided, Hybrid), against the serial oracle:
+exact split and exact multiset of each side.
+
+Small block sizes force many MakeSuccessorHeavy and Reorder levels at sizes the
+oracle checks in seconds; both role-swap paths (predecessors the minority and
+the majority) and the paper's base case (innermost prefix at most 5B) are
+covered, as are the full-size-style default parameters (B = 4096).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2004_12532_gb300 import binding as lp
+from paper_2004_12532_gb300 import inputs
+from tests.gpu_util import check_partition, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2004_12532_gb300 import build
+    build.build()
+    c = lp.Ctx(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 100, 5000, 65536 + 3, 1000003])
+@pytest.mark.parametrize("B", [16, 64, 4096])
+@pytest.mark.parametrize("q", [(1, 100), (1, 2), (7, 10), (99, 100)])
+def test_lowspace_paper_base(ctx, n, B, q):
+    host = inputs.uniform_u64(n, n * 7 + B)
+    pv = inputs.quantile_pivot(*q)
+    dev = to_dev(host)
+    t = lp.lp_lowspace_partition(ctx, dev, pv, B=B, base_keys=0)
+    check_partition(to_host(dev, np.uint64), host, t, oracle.count(host, pv), pv)
+
+
+@pytest.mark.parametrize("n", [(1 << 22) + 17, (1 << 23) + 5])
+@pytest.mark.parametrize("q", [(1, 2), (4, 5)])
+def test_lowspace_on_chip_base(ctx, n, q):
+    host = inputs.uniform_u64(n, n + q[0])
+    pv = inputs.quantile_pivot(*q)
+    dev = to_dev(host)
+    t = lp.lp_lowspace_partition(ctx, dev, pv, B=4096, base_keys=1 << 20)
+    check_partition(to_host(dev, np.uint64), host, t, oracle.count(host, pv), pv)
+
+
+@pytest.mark.parametrize("n", [5000, (1 << 21) + 9])
+def test_lowspace_u32(ctx, n):
+    host = inputs.uniform_u32(n, n)
+    pv = inputs.quantile_pivot(2, 3, 32)
+    dev = to_dev(host)
+    t = lp.lp_lowspace_partition(ctx, dev, pv, B=64)
+    check_partition(to_host(dev, np.uint32), host, t, oracle.count(host, pv), pv)
+
+
+@pytest.mark.parametrize("variant", [lp.LP_LOWSPACE, lp.LP_STRIDED, lp.LP_HYBRID])
+@pytest.mark.parametrize("n,offset", [(9000, 0), ((1 << 22) + 37, 1), ((1 << 23) + 1, 0)])
+def test_variants_u64(ctx, variant, n, offset):
+    host = inputs.uniform_u64(n, n + variant)
+    pv = inputs.quantile_pivot(3, 5)
+    buf = to_dev(np.concatenate([np.zeros(offset, np.uint64), host]))
+    view = buf[offset:]
+    t = lp.lp_partition_u64(ctx, view, pv, variant, seed=3)
+    check_partition(to_host(view, np.uint64), host, t, oracle.count(host, pv), pv)
+
+
+@pytest.mark.parametrize("variant", [lp.LP_LOWSPACE, lp.LP_STRIDED, lp.LP_HYBRID])
+def test_variants_u32_kv(ctx, variant):
+    n = (1 << 22) + 3
+    h32 = inputs.uniform_u32(n, 5)
+    pv32 = inputs.quantile_pivot(1, 2, 32)
+    d32 = to_dev(h32)
+    t = lp.lp_partition_u32(ctx, d32, pv32, variant, seed=1)
+    check_partition(to_host(d32, np.uint32), h32, t, oracle.count(h32, pv32), pv32)
+    keys = inputs.uniform_u64(n, 6)
+    vals = np.arange(n, dtype=np.uint64)
+    pv = inputs.quantile_pivot(1, 3)
+    dk, dv = to_dev(keys), to_dev(vals)
+    t = lp.lp_partition_kv_u64(ctx, dk, dv, pv, variant, seed=2)
+    ko, vo = to_host(dk, np.uint64), to_host(dv, np.uint64)
+    check_partition(ko, keys, t, oracle.count(keys, pv), pv)
+    assert np.array_equal(keys[vo.astype(np.int64)], ko)
+
+
+def test_strided_adversarial_period(ctx):
+    """Input aligned with the strides: the Strided step leaves a wide open
+    range, which the low-space cleanup must still finish."""
+    n = 1 << 22
+    host = np.where((np.arange(n) // 128) % 2432 < 1216, np.uint64(1), np.uint64(2**64 - 1))
+    dev = to_dev(host)
+    t = lp.lp_partition_u64(ctx, dev, 5, lp.LP_STRIDED)
+    check_partition(to_host(dev, np.uint64), host, t, oracle.count(host, 5), 5)
