@@ -131,6 +131,57 @@ lp_status lp_partition_kv_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t *vals,
                                     uint64_t n, uint64_t pivot, lp_variant variant,
                                     uint64_t seed, cudaStream_t stream, uint64_t *d_split);
 
+/* ------------------------------------------------------ batched partition
+ * Many independent partitions in one persistent cooperative launch: segment
+ * s is keys[0..n) of segs[s], partitioned by [x <= pivot] with the Recursive
+ * Smoothed Striding scheme (a step per round on its open range, the range
+ * finished on chip once one CTA can hold it).  Per segment the result is a
+ * partition with split t_s written to d_splits[s] (device, count entries),
+ * deterministic for a given batch, seed and tuning.  Segments must not
+ * overlap.  Scratch: about 48 bytes per segment plus 12 bytes per segment of
+ * plan space, held by ctx. */
+typedef struct {
+  uint64_t *keys; /* device pointer, naturally aligned */
+  uint64_t n;
+  uint64_t pivot;
+} lp_segment_u64;
+
+/* Knobs of the batched engine (0 = default); lp_autotune_batched_u64 picks
+ * them. */
+typedef struct {
+  uint32_t ctas;          /* CTAs of the persistent launch (<= lp_ctx_grid) */
+  uint32_t line_bytes;    /* line size b * 8 of the steps: 128 .. 1024 */
+  uint32_t min_chunks;    /* lines per group, at least */
+  uint32_t group_workers; /* groups per segment step, at most */
+} lp_batch_tuning;
+
+/* One-shot: copies the segment list (host) to the device and runs the batch on
+ * `stream` (asynchronous).  Uses the tuning stored in ctx. */
+lp_status lp_partition_batched_u64(lp_ctx *ctx, const lp_segment_u64 *segs, uint32_t count,
+                                   uint64_t seed, cudaStream_t stream, uint64_t *d_splits);
+
+/* A reusable batch: the segment list is uploaded once and the whole batch
+ * (set-up kernel, resets, persistent launch) is captured into a CUDA graph
+ * that lp_batch_launch replays -- one graph launch per batch, on any stream.
+ * The capture uses a stream of the library's own; `stream` is unused.  The
+ * key arrays may be refilled between launches; their addresses and sizes are
+ * fixed. */
+typedef struct lp_batch lp_batch;
+lp_status lp_batch_create(lp_ctx *ctx, const lp_segment_u64 *segs, uint32_t count,
+                          uint64_t seed, uint64_t *d_splits, cudaStream_t stream,
+                          lp_batch **out);
+lp_status lp_batch_launch(lp_batch *batch, cudaStream_t stream);
+lp_status lp_batch_destroy(lp_batch *batch);
+
+/* Autotuner: times candidate tunings on a synthetic batch with the given
+ * segment sizes (uniform keys, pivot = the middle of the key range), in a
+ * temporary buffer, and stores the fastest in ctx (also returned in *best).
+ * Takes a few hundred milliseconds; allocates and frees the temporary
+ * buffer. */
+lp_status lp_autotune_batched_u64(lp_ctx *ctx, const uint64_t *sizes, uint32_t count,
+                                  cudaStream_t stream, lp_batch_tuning *best);
+lp_status lp_ctx_set_batch_tuning(lp_ctx *ctx, const lp_batch_tuning *tuning);
+
 /* ------------------------------------------ Blocked-Prefix-Sum partition
  * The low-space partition of Sec. 3 with explicit block size: count the
  * predecessors (swapping the roles on the reversed array when they are the

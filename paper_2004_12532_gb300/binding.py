@@ -34,6 +34,15 @@ _p = C.c_void_p
 _i = C.c_int
 _pu64 = C.POINTER(C.c_uint64)
 
+class lp_segment_u64(C.Structure):
+    _fields_ = [("keys", C.c_void_p), ("n", C.c_uint64), ("pivot", C.c_uint64)]
+
+
+class lp_batch_tuning(C.Structure):
+    _fields_ = [("ctas", C.c_uint32), ("line_bytes", C.c_uint32), ("min_chunks", C.c_uint32),
+                ("group_workers", C.c_uint32)]
+
+
 _SIGS = {
     "lp_ctx_create": (_i, [C.POINTER(_p), _i]),
     "lp_ctx_destroy": (_i, [_p]),
@@ -57,6 +66,12 @@ _SIGS = {
     "lp_partition_u64_noalloc": (_i, [_p, _u64, _u64, _i, _u64, _p, _p]),
     "lp_lowspace_partition_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _p, _pu64]),
     "lp_lowspace_partition_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _p, _pu64]),
+    "lp_partition_batched_u64": (_i, [_p, _p, _u32, _u64, _p, _p]),
+    "lp_batch_create": (_i, [_p, _p, _u32, _u64, _p, _p, C.POINTER(_p)]),
+    "lp_batch_launch": (_i, [_p, _p]),
+    "lp_batch_destroy": (_i, [_p]),
+    "lp_autotune_batched_u64": (_i, [_p, _p, _u32, _p, _p]),
+    "lp_ctx_set_batch_tuning": (_i, [_p, _p]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -229,6 +244,68 @@ def lp_partition_u64_noalloc(keys, pivot, d_split, variant=LP_SMOOTHED, seed=0, 
                                         _stream(stream), s)
     if st != LP_OK:
         raise LPError(st, "lp_partition_u64_noalloc")
+
+
+def _segments(views, pivots):
+    arr = (lp_segment_u64 * len(views))()
+    for s, (v, p) in enumerate(zip(views, pivots)):
+        ptr, n = _dev_ptr(v, 64)
+        arr[s].keys = ptr.value if n else None
+        arr[s].n = n
+        arr[s].pivot = int(p)
+    return arr
+
+
+def lp_partition_batched_u64(ctx, views, pivots, d_splits, seed=0, stream=None):
+    """Partition every tensor in `views` (uint64 keys, non-overlapping) by its
+    pivot in one persistent launch; splits go to d_splits (device int64)."""
+    segs = _segments(views, pivots)
+    sp, m = _dev_ptr(d_splits, 64)
+    if m < len(views):
+        raise ValueError("d_splits too short")
+    ctx.check(lib().lp_partition_batched_u64(ctx.h, segs, len(views), int(seed),
+                                             _stream(stream), sp))
+
+
+class Batch:
+    """lp_batch: a segment list captured once into a CUDA graph, replayed."""
+
+    def __init__(self, ctx, views, pivots, d_splits, seed=0, stream=None):
+        self.ctx = ctx
+        self._segs = _segments(views, pivots)
+        sp, _ = _dev_ptr(d_splits, 64)
+        h = C.c_void_p()
+        ctx.check(lib().lp_batch_create(ctx.h, self._segs, len(views), int(seed), sp,
+                                        _stream(stream), C.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        self.ctx.check(lib().lp_batch_launch(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lp_autotune_batched_u64(ctx, sizes, stream=None):
+    arr = (C.c_uint64 * len(sizes))(*[int(x) for x in sizes])
+    best = lp_batch_tuning()
+    ctx.check(lib().lp_autotune_batched_u64(ctx.h, arr, len(sizes), _stream(stream),
+                                            C.byref(best)))
+    return {"ctas": best.ctas, "line_bytes": best.line_bytes, "min_chunks": best.min_chunks,
+            "group_workers": best.group_workers}
+
+
+def lp_ctx_set_batch_tuning(ctx, ctas=0, line_bytes=0, min_chunks=0, group_workers=0):
+    t = lp_batch_tuning(ctas, line_bytes, min_chunks, group_workers)
+    ctx.check(lib().lp_ctx_set_batch_tuning(ctx.h, C.byref(t)))
 
 
 def lp_lowspace_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):

@@ -8,41 +8,29 @@
 #include <string>
 
 #include "../../include/libpartition.h"
+#include "lp_batched.h"
+#include "lp_ctx.h"
 #include "lp_device.cuh"
 #include "lp_launch.h"
 #include "lp_plan.h"
 
-struct lp_ctx {
-  int device = 0;
-  uint32_t grid_u64 = 0, grid_u32 = 0, grid_kv = 0;
-  void* d_scratch = nullptr;      // fixed scratch: descriptors, status, split
-  size_t scratch_bytes = 0;
-  uint64_t* h_pinned = nullptr;   // 64 bytes of pinned host memory for read-back
-  uint64_t aux_bytes = 0;
-  uint64_t last_launches = 0;
-  std::string err;
-  lp::TaskScratch task{};
-  bool timing = false;
-  bool events_made = false;
-  bool last_timed = false;
-  cudaEvent_t ev[2];             // around the partition kernel of a timed call
-  cudaStream_t last_stream = nullptr;
-  void* d_var = nullptr;         // per-call scratch of the low-space partition (grown)
-  size_t var_bytes = 0;
-};
-
-namespace {
-
-lp_status fail(lp_ctx* c, lp_status s, const char* what) {
+lp_status lp_fail(lp_ctx* c, lp_status s, const char* what) {
   if (c) c->err = what;
   return s;
 }
 
-lp_status cuda_fail(lp_ctx* c, cudaError_t e, const char* where) {
+lp_status lp_cuda_fail(lp_ctx* c, cudaError_t e, const char* where) {
   if (c) {
     c->err = std::string(where) + ": " + cudaGetErrorString(e);
   }
   return LP_ERR_CUDA;
+}
+
+namespace {
+
+inline lp_status fail(lp_ctx* c, lp_status s, const char* what) { return lp_fail(c, s, what); }
+inline lp_status cuda_fail(lp_ctx* c, cudaError_t e, const char* where) {
+  return lp_cuda_fail(c, e, where);
 }
 
 lp_status status_to_lp(lp_ctx* c, uint32_t st) {
@@ -70,6 +58,8 @@ lp_status read_back(lp_ctx* c, cudaStream_t stream, uint64_t* split_out) {
   return status_to_lp(c, st);
 }
 
+}  // namespace
+
 // Grows the context's per-call scratch to at least `bytes` (a stream-ordered
 // free of the old buffer is not needed: the stream is synchronised first).
 lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream) {
@@ -77,14 +67,18 @@ lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream) {
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
   if (c->d_var) cudaFree(c->d_var);
+  if (c->d_batch) cudaFree(c->d_batch);
+  if (c->h_batch) cudaFreeHost(c->h_batch);
   c->d_var = nullptr;
   c->var_bytes = 0;
   e = cudaMalloc(&c->d_var, bytes);
   if (e != cudaSuccess) return fail(c, LP_ERR_OOM, "scratch allocation failed");
   c->var_bytes = bytes;
-  c->aux_bytes = c->scratch_bytes + c->var_bytes;
+  c->aux_bytes = c->scratch_bytes + c->var_bytes + c->batch_bytes;
   return LP_OK;
 }
+
+namespace {
 
 constexpr uint64_t kLowspaceBlock = 4096;  // B of the low-space partition (Sec. 5)
 
@@ -255,7 +249,9 @@ lp_status lp_ctx_create(lp_ctx** out, int device) {
   if (e != cudaSuccess) { delete c; return LP_ERR_CUDA; }
   if ((e = lp::streaming_grid<uint64_t, false>(device, &c->grid_u64)) != cudaSuccess ||
       (e = lp::streaming_grid<uint32_t, false>(device, &c->grid_u32)) != cudaSuccess ||
-      (e = lp::streaming_grid<uint64_t, true>(device, &c->grid_kv)) != cudaSuccess) {
+      (e = lp::streaming_grid<uint64_t, true>(device, &c->grid_kv)) != cudaSuccess ||
+      (e = lp::batched_prepare<uint64_t>()) != cudaSuccess ||
+      (e = lp::batched_prepare<uint32_t>()) != cudaSuccess) {
     delete c;
     return LP_ERR_CUDA;
   }
@@ -280,6 +276,8 @@ lp_status lp_ctx_destroy(lp_ctx* c) {
     for (int i = 0; i < 2; i++) cudaEventDestroy(c->ev[i]);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_var) cudaFree(c->d_var);
+  if (c->d_batch) cudaFree(c->d_batch);
+  if (c->h_batch) cudaFreeHost(c->h_batch);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   delete c;
   return LP_OK;

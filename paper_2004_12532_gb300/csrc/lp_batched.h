@@ -1,0 +1,65 @@
+// lp_batched.h -- internal interface of the batched partition engine
+// (lp_batched.cu): per-segment device records, scratch layout, tuning knobs.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "lp_launch.h"
+
+namespace lp {
+
+// One segment of a batch, in device memory.  The first three fields are the
+// caller's; the rest is the engine's state.
+struct SegDesc {
+  void* keys;
+  uint64_t n;
+  uint64_t pivot;
+  uint64_t seed;                    // per-segment seed of the offsets X
+  uint64_t h, be;                   // 16-byte aligned body [h, be)
+  uint64_t lo, hi;                  // open range of the current level
+  uint64_t b, g;                    // step parameters of the current level
+  unsigned long long vmin, vmax;    // this level's v_min / v_max (atomics)
+  unsigned long long count;         // this level's predecessor count (atomics)
+  unsigned long long body_count;    // predecessors of the body (from level 0)
+  unsigned long long t;             // the split, once done
+  uint32_t level, state;
+};
+
+struct BatchArgs {
+  uint64_t* splits;       // one split per segment (device)
+  uint32_t max_rounds;
+  uint64_t group_workers; // at most this many groups per segment step
+  uint32_t line_bytes;    // line size of the steps
+  uint32_t min_chunks;    // lines per group, at least
+};
+
+struct BatchScratch {
+  unsigned long long* wprefix;  // count + 1 task prefix entries
+  uint32_t* ctalist;            // count CTA-task segment ids
+  unsigned long long* totals;   // warp tasks, CTA tasks of the round
+  uint32_t* counters;           // task fetch counters
+  uint32_t* bar;                // grid barrier
+  uint32_t* status;
+};
+
+// Knobs the autotuner sets (0: default).
+struct BatchTuning {
+  uint32_t ctas;           // CTAs of the persistent launch
+  uint64_t group_workers;  // groups per segment step, at most
+  uint32_t line_bytes;     // 128..1024
+  uint32_t min_chunks;     // lines per group, at least
+};
+
+size_t batch_scratch_bytes(uint32_t count);
+BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint32_t* status);
+
+// Sets the batched kernel's shared-memory attribute (once per device, before
+// any stream capture).
+template <typename T>
+cudaError_t batched_prepare();
+
+template <typename T>
+cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
+                           const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg);
+
+}  // namespace lp

@@ -143,4 +143,24 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nbl
   return *flag_smem != 0u;
 }
 
+// Launches a kernel whose CTAs wait on one another (grid_barrier): the
+// cooperative launch attribute makes the runtime guarantee that all `grid`
+// CTAs are resident at once (or fail the launch), and this form of launch can
+// be captured into a CUDA graph.
+template <typename... P, typename... A>
+inline cudaError_t launch_cooperative(void (*kernel)(P...), uint32_t grid, uint32_t threads,
+                                      size_t smem, cudaStream_t stream, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace lp

@@ -336,12 +336,9 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
   uint64_t grid = cfg.grid;
   const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
   if (need < grid) grid = need ? need : 1;
-  TaskScratch Sv = S;
-  void* args[] = {&keys, &vals, &a, &Sv};
   if (cfg.events) cudaEventRecord(cfg.events[0], st);
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)partition_kernel<T, KV>,
-                                              dim3((unsigned)grid), dim3(R::Threads), args, smem,
-                                              st);
+  cudaError_t e = launch_cooperative(partition_kernel<T, KV>, (uint32_t)grid, R::Threads, smem,
+                                     st, keys, vals, a, S);
   cfg.launches++;
   if (cfg.events) cudaEventRecord(cfg.events[1], st);
   if (e != cudaSuccess) return e;
@@ -374,12 +371,9 @@ cudaError_t launch_first_level(T* keys, uint64_t* vals, uint64_t n, T pivot, uin
   uint64_t grid = cfg.grid;
   const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
   if (need < grid) grid = need ? need : 1;
-  TaskScratch Sv = S;
-  void* args[] = {&keys, &vals, &a, &Sv};
   if (cfg.events) cudaEventRecord(cfg.events[0], st);
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)partition_kernel<T, KV>,
-                                              dim3((unsigned)grid), dim3(R::Threads), args, smem,
-                                              st);
+  cudaError_t e = launch_cooperative(partition_kernel<T, KV>, (uint32_t)grid, R::Threads, smem,
+                                     st, keys, vals, a, S);
   cfg.launches++;
   if (cfg.events) cudaEventRecord(cfg.events[1], st);
   return e;

@@ -324,10 +324,7 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
   if (a.base_keys < 5 * B) a.base_keys = 0;  // the paper's base case decides
   e = cudaMemsetAsync(a.total, 0, 8, st);
   if (e != cudaSuccess) return e;
-  TaskScratch Sv = S;
-  void* args[] = {&keys, &vals, &a, &Sv};
-  e = cudaLaunchCooperativeKernel((const void*)lowspace_kernel<T, KV>, dim3(grid), dim3(kLT),
-                                  args, smem, st);
+  e = launch_cooperative(lowspace_kernel<T, KV>, grid, kLT, smem, st, keys, vals, a, S);
   cfg.launches++;
   return e;
 }

@@ -125,10 +125,10 @@ LP_HD uint64_t group_split_pos(const StepGeom& G, uint64_t i, uint64_t nl, uint6
 struct StepParams { uint64_t b, g; };
 
 LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t workers,
-                               uint32_t line_bytes) {
+                               uint32_t line_bytes, uint32_t min_chunks = kMinChunks) {
   StepParams P;
   P.b = line_bytes / key_bytes;
-  P.g = n / (P.b * kMinChunks);
+  P.g = n / (P.b * (min_chunks ? min_chunks : 1));
   if (P.g > workers) P.g = workers;
   if (P.g < 1) P.g = 1;
   return P;

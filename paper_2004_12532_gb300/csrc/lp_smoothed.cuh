@@ -370,9 +370,12 @@ __device__ uint32_t cta_partition_smem(T* __restrict__ keys, uint64_t* __restric
   uint64_t* sv = reinterpret_cast<uint64_t*>(
       smem + 128 + (((size_t)n * sizeof(T) + 15) & ~size_t(15)));
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  for (uint32_t q = tid; q < n; q += NT) {
-    sk[q] = keys[q];
-    if constexpr (KV) sv[q] = vals[q];
+  for (uint32_t q = tid; q < n; q += NT) {  // through L2: other CTAs may have written these
+    if constexpr (sizeof(T) == 8)
+      sk[q] = (T)__ldcg(reinterpret_cast<const unsigned long long*>(keys + q));
+    else
+      sk[q] = (T)__ldcg(reinterpret_cast<const unsigned int*>(keys + q));
+    if constexpr (KV) sv[q] = __ldcg(reinterpret_cast<const unsigned long long*>(vals + q));
   }
   __syncthreads();
   const uint32_t per = (n + NT - 1) / NT;
