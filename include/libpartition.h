@@ -182,6 +182,26 @@ lp_status lp_autotune_batched_u64(lp_ctx *ctx, const uint64_t *sizes, uint32_t c
                                   cudaStream_t stream, lp_batch_tuning *best);
 lp_status lp_ctx_set_batch_tuning(lp_ctx *ctx, const lp_batch_tuning *tuning);
 
+/* ------------------------------------------------------------ quicksort
+ * Sorts keys[0..n) ascending in place: the quicksort of Sec. 5 ("A Full
+ * Quicksort") built on the partition.  Level-synchronous: every level
+ * partitions all open subarrays (more than 4096 keys) at once through the
+ * batched engine, each by [x <= p] with p the median of three keys at
+ * positions drawn from `seed` and the subarray's place; a subarray where no
+ * key exceeds p is partitioned again by [x < p] and the keys equal to p are
+ * final (the paper is silent on pivots and duplicates).  Subarrays of at most
+ * 4096 keys are sorted by one CTA each in shared memory.  The result is the
+ * sorted array, whatever the seed; the seed only changes the work done.
+ * Scratch: about 90 bytes per 4096 keys plus ~2.4 MB at most of per-segment
+ * records, held by ctx.  Synchronises `stream` once or twice per level (the
+ * host reads the list sizes) and before returning.  Errors: LP_ERR_INVALID_ARG
+ * (null or misaligned array), LP_ERR_OOM, LP_ERR_TIMEOUT (a bounded device
+ * wait gave up), LP_ERR_CUDA. */
+lp_status lp_quicksort_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t seed,
+                           cudaStream_t stream);
+lp_status lp_quicksort_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint64_t seed,
+                           cudaStream_t stream);
+
 /* ------------------------------------------ Blocked-Prefix-Sum partition
  * The low-space partition of Sec. 3 with explicit block size: count the
  * predecessors (swapping the roles on the reversed array when they are the

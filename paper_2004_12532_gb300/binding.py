@@ -72,6 +72,8 @@ _SIGS = {
     "lp_batch_destroy": (_i, [_p]),
     "lp_autotune_batched_u64": (_i, [_p, _p, _u32, _p, _p]),
     "lp_ctx_set_batch_tuning": (_i, [_p, _p]),
+    "lp_quicksort_u64": (_i, [_p, _p, _u64, _u64, _p]),
+    "lp_quicksort_u32": (_i, [_p, _p, _u64, _u64, _p]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -306,6 +308,14 @@ def lp_autotune_batched_u64(ctx, sizes, stream=None):
 def lp_ctx_set_batch_tuning(ctx, ctas=0, line_bytes=0, min_chunks=0, group_workers=0):
     t = lp_batch_tuning(ctas, line_bytes, min_chunks, group_workers)
     ctx.check(lib().lp_ctx_set_batch_tuning(ctx.h, C.byref(t)))
+
+
+def lp_quicksort(ctx, keys, seed=0, stream=None):
+    """Sort a uint64 or uint32 device tensor ascending in place."""
+    bits = keys.element_size() * 8
+    p, n = _dev_ptr(keys, bits)
+    f = lib().lp_quicksort_u64 if bits == 64 else lib().lp_quicksort_u32
+    ctx.check(f(ctx.h, p, n, int(seed), _stream(stream)))
 
 
 def lp_lowspace_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):

@@ -67,8 +67,6 @@ lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream) {
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
   if (c->d_var) cudaFree(c->d_var);
-  if (c->d_batch) cudaFree(c->d_batch);
-  if (c->h_batch) cudaFreeHost(c->h_batch);
   c->d_var = nullptr;
   c->var_bytes = 0;
   e = cudaMalloc(&c->d_var, bytes);
@@ -250,8 +248,8 @@ lp_status lp_ctx_create(lp_ctx** out, int device) {
   if ((e = lp::streaming_grid<uint64_t, false>(device, &c->grid_u64)) != cudaSuccess ||
       (e = lp::streaming_grid<uint32_t, false>(device, &c->grid_u32)) != cudaSuccess ||
       (e = lp::streaming_grid<uint64_t, true>(device, &c->grid_kv)) != cudaSuccess ||
-      (e = lp::batched_prepare<uint64_t>()) != cudaSuccess ||
-      (e = lp::batched_prepare<uint32_t>()) != cudaSuccess) {
+      (e = lp::batched_prepare<uint64_t>(device, &c->grid_batch_u64)) != cudaSuccess ||
+      (e = lp::batched_prepare<uint32_t>(device, &c->grid_batch_u32)) != cudaSuccess) {
     delete c;
     return LP_ERR_CUDA;
   }

@@ -9,6 +9,7 @@
 
 #include "lp_batched.h"
 #include "lp_ctx.h"
+#include "lp_device.cuh"
 
 struct lp_batch {
   lp_ctx* ctx = nullptr;
@@ -50,6 +51,7 @@ void fill_records(std::vector<lp::SegDesc>& out, const lp_segment_u64* segs, uin
     out[s].keys = segs[s].keys;
     out[s].n = segs[s].n;
     out[s].pivot = segs[s].pivot;
+    out[s].salt = s;  // a segment's offsets X follow from the seed and its index
   }
 }
 
@@ -57,10 +59,10 @@ size_t records_bytes(uint32_t count) {
   return ((size_t)count * sizeof(lp::SegDesc) + 255) / 256 * 256;
 }
 
-lp_status tuned_grid(lp_ctx* c, const lp::BatchTuning& t, uint32_t* grid) {
-  *grid = c->grid_u64;
-  if (t.ctas && t.ctas < *grid) *grid = t.ctas;
-  return LP_OK;
+// CTAs of a batched launch: the tuned count, at most every resident CTA
+uint32_t tuned_grid(const lp_ctx* c, const lp::BatchTuning& t, size_t key_bytes) {
+  const uint32_t full = key_bytes == 8 ? c->grid_batch_u64 : c->grid_batch_u32;
+  return t.ctas && t.ctas < full ? t.ctas : full;
 }
 
 }  // namespace
@@ -117,9 +119,7 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
   lp::BatchScratch B = lp::carve_batch_scratch(static_cast<unsigned char*>(c->d_batch) + rec,
                                                count, c->task.bar, c->task.status);
   const lp::BatchTuning tune = to_internal(c->tuning);
-  uint32_t grid = 0;
-  tuned_grid(c, tune, &grid);
-  lp::LaunchCfg cfg{grid, stream, 0, nullptr};
+  lp::LaunchCfg cfg{tuned_grid(c, tune, 8), stream, 0, nullptr};
   c->last_timed = false;
   c->last_stream = stream;
   e = lp::launch_batched<uint64_t>(reinterpret_cast<lp::SegDesc*>(c->d_batch), count, seed,
@@ -164,8 +164,7 @@ lp_status lp_batch_create(lp_ctx* c, const lp_segment_u64* segs, uint32_t count,
   // capture set-up, resets and the persistent launch into one graph, on a
   // stream of our own (the legacy default stream cannot be captured); the
   // graph is later launched on the caller's stream
-  uint32_t grid = 0;
-  tuned_grid(c, b->tune, &grid);
+  const uint32_t grid = tuned_grid(c, b->tune, 8);
   (void)stream;
   cudaStream_t cap = nullptr;
   e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -235,7 +234,7 @@ lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t cou
   const lp_batch_tuning saved = c->tuning;
   const uint32_t line_opts[] = {512, 1024};
   const uint32_t chunk_opts[] = {16, 32, 64, 128};
-  const uint32_t cta_opts[] = {0, c->grid_u64 / 2};
+  const uint32_t cta_opts[] = {0, c->grid_batch_u64 / 2};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -271,6 +270,56 @@ lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t cou
   c->tuning = st == LP_OK ? best_t : saved;
   if (best) *best = c->tuning;
   return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, cudaStream_t stream) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->err.clear();
+  c->last_launches = 0;
+  if (n > 0 && !keys) return lp_fail(c, LP_ERR_INVALID_ARG, "null array");
+  if ((reinterpret_cast<uintptr_t>(keys) % sizeof(T)) != 0)
+    return lp_fail(c, LP_ERR_INVALID_ARG, "array not aligned");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "cudaSetDevice");
+  if (n < 2) return LP_OK;
+  lp_status ls = ensure_var(c, lp::quicksort_scratch_bytes(n), stream);
+  if (ls != LP_OK) return ls;
+  e = cudaMemsetAsync(c->task.status, 0, 4, stream);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "reset status");
+  const lp::BatchTuning tune = to_internal(c->tuning);
+  lp::LaunchCfg cfg{tuned_grid(c, tune, sizeof(T)), stream, 0, nullptr};
+  c->last_timed = false;
+  c->last_stream = stream;
+  e = lp::launch_quicksort<T>(keys, n, seed, c->d_var, c->h_pinned, tune, c->task.bar,
+                              c->task.status, cfg, nullptr);
+  c->last_launches = cfg.launches;
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "quicksort");
+  e = cudaMemcpyAsync(c->h_pinned, c->task.status, 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "read status");
+  const uint32_t st = (uint32_t)(c->h_pinned[0] & 0xffffffffu);
+  if (st & lp::kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (st) return lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed");
+  return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_quicksort_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,
+                           cudaStream_t stream) {
+  return quicksort_impl<uint64_t>(c, keys, n, seed, stream);
+}
+
+lp_status lp_quicksort_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint64_t seed,
+                           cudaStream_t stream) {
+  return quicksort_impl<uint32_t>(c, keys, n, seed, stream);
 }
 
 }  // extern "C"

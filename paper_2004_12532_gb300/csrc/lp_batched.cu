@@ -290,7 +290,9 @@ __global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed)
   d.hi = d.be;
   d.level = 0;
   d.state = kSegOpen;
-  d.seed = sm_stream(seed, s);
+  // the offsets X of a segment depend on the batch seed and the segment's
+  // salt only, not on its place in the list
+  d.seed = sm_stream(seed, d.salt);
   d.vmin = ~0ull;
   d.vmax = 0ull;
   d.count = 0ull;
@@ -345,12 +347,23 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
 }
 
 template <typename T>
-cudaError_t batched_prepare() {
-  return cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)level_smem_bytes<T, false>());
+cudaError_t batched_prepare(int device, uint32_t* grid) {
+  using R = Tr<T, false>;
+  const size_t smem = level_smem_bytes<T, false>();
+  cudaError_t e = cudaFuncSetAttribute(batched_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int sms = 0, per = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<T>, R::Threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  *grid = (uint32_t)(sms * per);  // every CTA resident: the grid barrier needs it
+  return cudaSuccess;
 }
-template cudaError_t batched_prepare<uint64_t>();
-template cudaError_t batched_prepare<uint32_t>();
+template cudaError_t batched_prepare<uint64_t>(int, uint32_t*);
+template cudaError_t batched_prepare<uint32_t>(int, uint32_t*);
 
 template cudaError_t launch_batched<uint64_t>(SegDesc*, uint32_t, uint64_t, uint64_t*,
                                               const BatchScratch&, const BatchTuning&,

@@ -8,13 +8,14 @@
 
 namespace lp {
 
-// One segment of a batch, in device memory.  The first three fields are the
+// One segment of a batch, in device memory.  The first four fields are the
 // caller's; the rest is the engine's state.
 struct SegDesc {
   void* keys;
   uint64_t n;
   uint64_t pivot;
-  uint64_t seed;                    // per-segment seed of the offsets X
+  uint64_t salt;                    // names the segment: its offsets X depend on it
+  uint64_t seed;                    // per-segment seed of the offsets X (batch seed, salt)
   uint64_t h, be;                   // 16-byte aligned body [h, be)
   uint64_t lo, hi;                  // open range of the current level
   uint64_t b, g;                    // step parameters of the current level
@@ -54,12 +55,22 @@ size_t batch_scratch_bytes(uint32_t count);
 BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint32_t* status);
 
 // Sets the batched kernel's shared-memory attribute (once per device, before
-// any stream capture).
+// any stream capture) and returns its cooperative grid: SMs x resident CTAs.
 template <typename T>
-cudaError_t batched_prepare();
+cudaError_t batched_prepare(int device, uint32_t* grid);
 
 template <typename T>
 cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
                            const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg);
+
+// Quicksort on the batched partition (lp_quicksort.cu).  `host_words`: 16
+// bytes of pinned host memory for list sizes; synchronises `cfg.stream` once
+// or twice per level.
+size_t quicksort_scratch_bytes(uint64_t n);
+
+template <typename T>
+cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* host_words,
+                             const BatchTuning& tune, uint32_t* bar, uint32_t* status,
+                             LaunchCfg& cfg, uint32_t* levels_out);
 
 }  // namespace lp

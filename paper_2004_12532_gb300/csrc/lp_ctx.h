@@ -12,6 +12,7 @@
 struct lp_ctx {
   int device = 0;
   uint32_t grid_u64 = 0, grid_u32 = 0, grid_kv = 0;
+  uint32_t grid_batch_u64 = 0, grid_batch_u32 = 0;  // cooperative grids of the batched kernel
   void* d_scratch = nullptr;      // fixed scratch: descriptors, status, split
   size_t scratch_bytes = 0;
   uint64_t* h_pinned = nullptr;   // 64 bytes of pinned host memory for read-back

@@ -1,0 +1,143 @@
+"""GPU parity of the quicksort on the partition (Sec. 5, "A Full Quicksort").
+
+The sorted array is unique, so the GPU result must equal the oracle's serial
+quicksort byte for byte: uniform, sorted, reverse-sorted and heavy-duplicate
+inputs (the four inputs of the n = 2^28 workload), uint64 and uint32, sizes
+around the shared-memory cut (4096 keys), the one-CTA finish and several
+partition levels, and views at odd 8-byte offsets.  At the workload's full
+size the result is checked by properties: non-decreasing, and equal to a
+library sort of the input.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2004_12532_gb300 import binding as lp
+from paper_2004_12532_gb300 import inputs
+from tests.gpu_util import to_dev, to_host, unsigned_key
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2004_12532_gb300 import build
+    build.build()
+    c = lp.Ctx(0)
+    yield c
+    c.close()
+
+
+def make(kind, n, seed, dtype=np.uint64):
+    if dtype == np.uint32:
+        if kind == "uniform":
+            return inputs.uniform_u32(n, seed)
+        if kind == "dup16":
+            return (inputs.uniform_u32(n, seed) & np.uint32(15)).astype(np.uint32)
+        raise ValueError(kind)
+    if kind == "uniform":
+        return inputs.uniform_u64(n, seed)
+    if kind == "sorted":
+        return inputs.sorted_u64(n, seed)
+    if kind == "reverse":
+        return inputs.reverse_sorted_u64(n, seed)
+    if kind == "dup16":
+        return inputs.heavy_duplicates_u64(n, seed, 16)
+    if kind == "equal":
+        return np.full(n, np.uint64(0x1234), dtype=np.uint64)
+    if kind == "zeros":
+        return np.zeros(n, dtype=np.uint64)
+    if kind == "max":
+        return np.full(n, np.uint64(2**64 - 1), dtype=np.uint64)
+    if kind == "two":
+        return np.where(inputs.uniform_u64(n, seed) & np.uint64(1), np.uint64(0),
+                        np.uint64(2**64 - 1)).astype(np.uint64)
+    raise ValueError(kind)
+
+
+def run_and_compare(ctx, host, seed=5):
+    ref = host.copy()
+    oracle.quicksort(ref, seed)
+    assert np.array_equal(ref, np.sort(host))  # the oracle sorts
+    d = to_dev(host)
+    lp.lp_quicksort(ctx, d, seed=seed)
+    torch.cuda.synchronize()
+    out = to_host(d, host.dtype)
+    assert np.array_equal(out, ref)
+
+
+SIZES = [0, 1, 2, 3, 17, 4095, 4096, 4097, 8191, 12289, 65536 + 7, 1 << 20, (1 << 21) + 333]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_uniform_u64_sizes(ctx, n):
+    run_and_compare(ctx, make("uniform", n, 100 + n))
+
+
+@pytest.mark.parametrize("kind", ["sorted", "reverse", "dup16", "equal", "zeros", "max", "two"])
+@pytest.mark.parametrize("n", [5000, 300000])
+def test_patterns_u64(ctx, kind, n):
+    run_and_compare(ctx, make(kind, n, 7 + n))
+
+
+@pytest.mark.parametrize("kind", ["uniform", "dup16"])
+@pytest.mark.parametrize("n", [1, 4096, 4097, 100003, 1 << 20])
+def test_u32(ctx, kind, n):
+    run_and_compare(ctx, make(kind, n, 31 + n, np.uint32))
+
+
+@pytest.mark.parametrize("off", [1, 3])
+def test_unaligned_view(ctx, off):
+    n = 200001
+    host = make("uniform", n + off + 2, 9)
+    d = to_dev(host)
+    view = d[off:off + n]
+    lp.lp_quicksort(ctx, view, seed=3)
+    torch.cuda.synchronize()
+    out = to_host(d, np.uint64)
+    ref = host.copy()
+    oracle.quicksort(ref[off:off + n], 3)
+    assert np.array_equal(out, ref)  # keys outside the view unchanged
+
+
+def test_seed_independent_result(ctx):
+    host = make("dup16", 1 << 19, 4)
+    outs = []
+    for seed in (0, 1, 12345):
+        d = to_dev(host)
+        lp.lp_quicksort(ctx, d, seed=seed)
+        outs.append(to_host(d, np.uint64))
+    assert all(np.array_equal(outs[0], o) for o in outs)
+    assert np.array_equal(outs[0], np.sort(host))
+
+
+def test_aux_memory_small(ctx):
+    n = 1 << 24
+    d = torch.empty(n, dtype=torch.int64, device="cuda")
+    lp.lp_fill_uniform_u64(d, 77)
+    lp.lp_quicksort(ctx, d, seed=1)
+    key = unsigned_key(d)
+    assert bool((key[1:] >= key[:-1]).all())
+    # lists and per-segment records of the quicksort: well under 1% of 128 MiB
+    # (the context's fixed scratch and earlier calls' buffers are included)
+    assert ctx.aux_bytes < 0.01 * n * 8
+
+
+@pytest.mark.parametrize("kind", ["uniform", "sorted", "reverse", "dup16"])
+def test_full_size_2pow28(ctx, kind):
+    """The n = 2^28 uint64 workload: sorted, and equal to a library sort."""
+    n = 1 << 28
+    d = torch.empty(n, dtype=torch.int64, device="cuda")
+    # the same patterns as the smaller cases, built on the device
+    lp.lp_fill_uniform_u64(d, 2024)
+    if kind == "sorted":
+        d.copy_(unsigned_key(torch.sort(unsigned_key(d)).values))
+    elif kind == "reverse":
+        d.copy_(unsigned_key(torch.sort(unsigned_key(d), descending=True).values))
+    elif kind == "dup16":
+        d.bitwise_and_(15)
+    expect = torch.sort(unsigned_key(d)).values
+    lp.lp_quicksort(ctx, d, seed=11)
+    got = unsigned_key(d)
+    assert torch.equal(got, expect)
