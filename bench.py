@@ -61,6 +61,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--seed", type=int, default=0xC0FF2)
+    ap.add_argument("--workload", choices=["partition", "quicksort", "batched"],
+                    default="partition",
+                    help="partition (default): one 2^30-key partition; quicksort: 2^28 uint64 "
+                         "sort; batched: 4096 partitions of log-uniform sizes in one graph")
+    ap.add_argument("--input", choices=["uniform", "sorted", "reverse", "dup16"],
+                    default="uniform", help="quicksort input")
+    ap.add_argument("--instances", type=int, default=4096, help="batched: instance count")
     return ap.parse_args()
 
 
@@ -178,6 +185,10 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "quicksort":
+        return run_reference_sort(args)
+    if args.workload == "batched":
+        return run_reference_batched(args)
     import oracle
     pivot = inputs.quantile_pivot(1, 2)
     log2s = min(args.log2n, 26)
@@ -205,6 +216,57 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def reference_line(args, metric, value, unit, ms, workload, oracle_kind, sample):
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": workload, "oracle": oracle_kind},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_reference_sort(args):
+    import oracle
+    log2s = min(args.log2n, 22)
+    n = 1 << log2s
+    for w in range(args.warmup):
+        oracle.quicksort(host_sort_input(args.input, n, args.seed + 1000 + w), w)
+    total = 0.0
+    for k in range(args.steps):
+        a = host_sort_input(args.input, n, args.seed + k)
+        t0 = time.perf_counter()
+        oracle.quicksort(a, k)
+        total += time.perf_counter() - t0
+    ms = total / args.steps * 1e3
+    reference_line(args, "quicksort keys/s (uint64, n=2^%d, %s)" % (args.log2n, args.input),
+                   n / (ms / 1e3) / 1e9, "Gkeys/s", ms,
+                   "quicksort u64 n=2^%d input=%s" % (args.log2n, args.input),
+                   "serial quicksort (CPU)",
+                   "2^%d uint64 keys per step, same input kind" % log2s)
+
+
+def run_reference_batched(args):
+    sizes, _, _ = batch_layout(args.instances, args.seed)
+    for w in range(args.warmup):
+        cpu_oracle_batch(sizes[:8], args.seed + w, 0.5)
+    vals = []
+    keys = 0
+    for k in range(args.steps):
+        v, done, inst = cpu_oracle_batch(sizes, args.seed + k, 2.0)
+        vals.append(v)
+        keys += done
+    v = statistics.mean(vals)
+    ms = keys / args.steps / (v * 1e9) * 1e3
+    reference_line(args, "batched partition keys/s (%d uint64 instances, sizes log-uniform "
+                   "[2^8, 2^22])" % args.instances, v, "Gkeys/s", ms,
+                   "batched partition, %d instances" % args.instances,
+                   "serial two-pointer partition per instance (CPU)",
+                   "about 2 s of instances per step, in batch order")
 
 
 def run_ours(args):
@@ -379,12 +441,364 @@ def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):
             "path": "pinned host -> device, lp_partition_u64_async, device -> pinned host"}
 
 
+# ---------------------------------------------------------------- quicksort
+
+def unsigned_order(t):
+    """Signed view of uint64 bits whose order is the unsigned order (an involution)."""
+    import torch
+    return t ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=t.device)
+
+
+def fill_sort_input(lp, keys, kind, seed):
+    import torch
+    lp.lp_fill_uniform_u64(keys, seed)
+    if kind == "sorted":
+        keys.copy_(unsigned_order(torch.sort(unsigned_order(keys)).values))
+    elif kind == "reverse":
+        keys.copy_(unsigned_order(torch.sort(unsigned_order(keys), descending=True).values))
+    elif kind == "dup16":
+        keys.bitwise_and_(15)
+
+
+def host_sort_input(kind, n, seed):
+    if kind == "uniform":
+        return inputs.uniform_u64(n, seed)
+    if kind == "sorted":
+        return inputs.sorted_u64(n, seed)
+    if kind == "reverse":
+        return inputs.reverse_sorted_u64(n, seed)
+    return inputs.heavy_duplicates_u64(n, seed, 16)
+
+
+def cpu_oracle_sort(kind, log2n, seed, min_seconds=8.0, max_reps=5):
+    import oracle
+    n = 1 << log2n
+    times = []
+    t_start = time.time()
+    for r in range(max_reps):
+        a = host_sort_input(kind, n, seed + r)
+        t0 = time.perf_counter()
+        oracle.quicksort(a, r)
+        times.append(time.perf_counter() - t0)
+        if time.time() - t_start > min_seconds and len(times) >= 2:
+            break
+    med = statistics.median(times)
+    return n / med / 1e9, n, len(times), med
+
+
+def init_dist(local, ws):
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+
+def max_over_ranks(ws, ms):
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def run_quicksort(args):
+    import torch
+    ws, rank, local = dist_env()
+    init_dist(local, ws)
+    from paper_2004_12532_gb300 import binding as lp
+    n = 1 << args.log2n
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    ctx = lp.Ctx(local)
+    ctx.set_timing(True)
+    stream = torch.cuda.current_stream()
+    seed0 = args.seed + 7919 * rank
+    for w in range(args.warmup):
+        fill_sort_input(lp, keys, args.input, seed0 + 100000 + w)
+        lp.lp_quicksort(ctx, keys, seed=w)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms, stats, launches = [], [], 0
+    wall0 = time.perf_counter()
+    clocks.start()
+    for k in range(args.steps):
+        fill_sort_input(lp, keys, args.input, seed0 + k)  # untimed; 2 GiB > L2
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        lp.lp_quicksort(ctx, keys, seed=k)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        stats.append(ctx.sort_stats())
+        launches += ctx.last_launches
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall_s = time.perf_counter() - wall0
+    clk = clocks.stop()
+    key = unsigned_order(keys)
+    sorted_ok = bool((key[1:] >= key[:-1]).all())
+    ms = sum(step_ms) / len(step_ms)
+    ms_all = max_over_ranks(ws, ms)
+    value = ws * n / (ms_all / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    pk = sum(s["partition_keys"] for s in stats) / len(stats)
+    pms = sum(s["partition_ms"] for s in stats) / len(stats)
+    sk = sum(s["sort_keys"] for s in stats) / len(stats)
+    sms = sum(s["sort_ms"] for s in stats) / len(stats)
+    achieved = 2 * 8 * pk / (pms / 1e3) / 1e9
+    result = {
+        "metric": "quicksort keys/s (uint64, n=2^%d, %s)" % (args.log2n, args.input),
+        "value": value, "unit": "Gkeys/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (SplitMix64 uniform keys, seeded; sorted / reverse / mod 16 "
+                "derived from them)",
+        "config": {"workload": "quicksort u64 n=2^%d input=%s" % (args.log2n, args.input),
+                   "n": n, "input": args.input,
+                   "l2": "2 GiB input, regenerated on device between steps",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "batched_kernel<uint64_t> (every partition level, "
+                               "with its set-up launches)",
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_step": 2 * 8 * pk, "ms_per_step": pms,
+                     "sort_kernel": {"achieved": 2 * 8 * sk / (sms / 1e3) / 1e9 if sms else None,
+                                     "ms_per_step": sms, "keys": sk}},
+        "levels": stats[-1]["levels"],
+        "partition_keys_per_key": pk / n,
+        "gpu_launches": launches,
+        "sorted_last_step": sorted_ok,
+        "aux_bytes": ctx.aux_bytes,
+        "wall_s_timed_region": wall_s,
+    }
+    if clk:
+        result["clocks"] = clk
+    if not args.no_e2e:
+        host_in = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        host_out = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        fill_sort_input(lp, keys, args.input, seed0 + 555)
+        host_in.copy_(keys)
+        torch.cuda.synchronize()
+        times = []
+        for k in range(max(1, args.e2e_steps)):
+            ev0.record(stream)
+            keys.copy_(host_in, non_blocking=True)
+            lp.lp_quicksort(ctx, keys, seed=k)
+            host_out.copy_(keys, non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+        e_ms = sum(times) / len(times)
+        result["e2e"] = {"value": n / (e_ms / 1e3) / 1e9, "unit": "Gkeys/s", "ms_per_step": e_ms,
+                         "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                         "path": "pinned host -> device, lp_quicksort_u64, device -> pinned host"}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, ns, reps, med = cpu_oracle_sort(args.input, min(args.log2n, 22), args.seed)
+        result["cpu_baseline"] = {
+            "value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": "2^%d uint64 keys, same input kind, median of %d runs (%.2f s each) of "
+                      "the serial quicksort" % (int(np.log2(ns)), reps, med),
+            "host_cores_available": os.cpu_count()}
+    if rank == 0:
+        print(json.dumps(result))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- batched
+
+def batch_layout(count, seed):
+    """Sizes log-uniform in [2^8, 2^22] and 16-byte aligned offsets in one buffer."""
+    sizes = inputs.log_uniform_sizes(count, seed, 8, 22)
+    offs, tot = [], 0
+    for m in sizes:
+        offs.append(tot)
+        tot += (int(m) + 1) & ~1
+    return sizes, offs, tot
+
+
+def cpu_oracle_batch(sizes, seed, budget_s):
+    """The serial oracle over the batch's instances in order, for about budget_s
+    seconds of partition time; returns (Gkeys/s, keys, instances)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    spent, done, inst = 0.0, 0, 0
+    for s, m in enumerate(sizes):
+        a = inputs.uniform_u64(int(m), seed + s)
+        p = int(a[int(rng.integers(0, m))])
+        t0 = time.perf_counter()
+        oracle.partition(a, p)
+        spent += time.perf_counter() - t0
+        done += int(m)
+        inst += 1
+        if spent > budget_s:
+            break
+    return done / spent / 1e9, done, inst
+
+
+def run_batched(args):
+    import torch
+    ws, rank, local = dist_env()
+    init_dist(local, ws)
+    from paper_2004_12532_gb300 import binding as lp
+    count = args.instances
+    sizes, offs, tot = batch_layout(count, args.seed)
+    keys_total = int(sum(int(m) for m in sizes))
+    buf = torch.empty(tot, dtype=torch.int64, device="cuda")
+    seed0 = args.seed + 7919 * rank
+    # every step partitions the same seeded input (regenerated on the device,
+    # 14 GB > L2), so each pivot stays a seeded random element of its segment
+    lp.lp_fill_uniform_u64(buf, seed0)
+    rng = np.random.default_rng(args.seed)
+    pick = [o + int(rng.integers(0, m)) for o, m in zip(offs, sizes)]
+    pv = buf[torch.tensor(pick, dtype=torch.int64, device="cuda")].cpu().numpy()
+    pivots = [int(x) & 0xFFFFFFFFFFFFFFFF for x in pv]
+    views = [buf[o:o + int(m)] for o, m in zip(offs, sizes)]
+    splits = torch.zeros(count, dtype=torch.int64, device="cuda")
+    splits_plain = torch.zeros(count, dtype=torch.int64, device="cuda")
+    ctx = lp.Ctx(local)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    tuning = lp.lp_autotune_batched_u64(ctx, [int(m) for m in sizes])
+    tune_s = time.perf_counter() - t0
+    batch = lp.Batch(ctx, views, pivots, splits, seed=1)
+    for w in range(args.warmup):
+        lp.lp_fill_uniform_u64(buf, seed0)
+        batch.launch()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    g_ms, streamed, launches = [], [], 0
+    wall0 = time.perf_counter()
+    clocks.start()
+    for k in range(args.steps):
+        lp.lp_fill_uniform_u64(buf, seed0)
+        ev0.record(stream)
+        batch.launch()
+        ev1.record(stream)
+        ev1.synchronize()
+        g_ms.append(ev0.elapsed_time(ev1))
+        launches += ctx.last_launches
+        streamed.append(batch.streamed_keys())
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall_s = time.perf_counter() - wall0
+    clk = clocks.stop()
+    # the same instances as separate plain launches (lp_partition_u64_async each)
+    p_ms, p_launches = [], 0
+    for k in range(max(1, min(args.steps, 3))):
+        lp.lp_fill_uniform_u64(buf, seed0)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for s in range(count):
+            lp.lp_partition_u64_async(ctx, views[s], pivots[s], splits_plain[s:s + 1], seed=k)
+            p_launches += ctx.last_launches
+        ev1.record(stream)
+        ev1.synchronize()
+        p_ms.append(ev0.elapsed_time(ev1))
+    same_splits = bool(torch.equal(splits, splits_plain))
+    ms = sum(g_ms) / len(g_ms)
+    ms_all = max_over_ranks(ws, ms)
+    value = ws * keys_total / (ms_all / 1e3) / 1e9
+    plain_ms = sum(p_ms) / len(p_ms)
+    peak, peak_kind = measured_peaks()
+    sk = sum(streamed) / len(streamed)
+    achieved = 2 * 8 * sk / (ms / 1e3) / 1e9
+    result = {
+        "metric": "batched partition keys/s (%d uint64 instances, sizes log-uniform "
+                  "[2^8, 2^22])" % count,
+        "value": value, "unit": "Gkeys/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (SplitMix64 uniform keys, seeded; pivot = seeded random element "
+                "of each instance)",
+        "config": {"workload": "batched partition, %d instances, %d keys in all" % (
+                       count, keys_total),
+                   "instances": count, "keys": keys_total, "tuning": tuning,
+                   "autotune_s": tune_s,
+                   "l2": "inputs larger than L2 (%.1f GB), regenerated on device between steps"
+                         % (8 * keys_total / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "batched_kernel<uint64_t> (one graph: set-up kernel + "
+                               "persistent kernel)",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": 2 * 8 * sk,
+                     "ms_per_launch": ms},
+        "per_instance_launches": {"value": keys_total / (plain_ms / 1e3) / 1e9,
+                                  "unit": "Gkeys/s", "ms_per_step": plain_ms,
+                                  "calls": count, "gpu_launches": p_launches // len(p_ms),
+                                  "speedup_of_batched": plain_ms / ms,
+                                  "same_splits": same_splits},
+        "streamed_keys_per_key": sk / keys_total,
+        "gpu_launches": launches,
+        "aux_bytes": ctx.aux_bytes,
+        "wall_s_timed_region": wall_s,
+    }
+    if clk:
+        result["clocks"] = clk
+    if not args.no_e2e:
+        host_in = torch.empty(tot, dtype=torch.int64, pin_memory=True)
+        host_out = torch.empty(tot, dtype=torch.int64, pin_memory=True)
+        host_splits = torch.empty(count, dtype=torch.int64, pin_memory=True)
+        lp.lp_fill_uniform_u64(buf, seed0)
+        host_in.copy_(buf)
+        torch.cuda.synchronize()
+        times = []
+        for k in range(max(1, args.e2e_steps)):
+            ev0.record(stream)
+            buf.copy_(host_in, non_blocking=True)
+            batch.launch()
+            host_out.copy_(buf, non_blocking=True)
+            host_splits.copy_(splits, non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+        e_ms = sum(times) / len(times)
+        result["e2e"] = {"value": keys_total / (e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
+                         "ms_per_step": e_ms, "h2d_bytes_per_step": 8 * tot,
+                         "d2h_bytes_per_step": 8 * tot + 8 * count,
+                         "path": "pinned host -> device, graph launch of the batch, "
+                                 "device -> pinned host (keys and splits)"}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, done, inst = cpu_oracle_batch(sizes, args.seed, 10.0)
+        result["cpu_baseline"] = {
+            "value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": "the first %d instances (%d keys), serial two-pointer partition, pivot "
+                      "a seeded element of each" % (inst, done),
+            "host_cores_available": os.cpu_count()}
+    batch.close()
+    if rank == 0:
+        print(json.dumps(result))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.log2n is None:
-        args.log2n = {"u64": 30, "u32": 31, "kv": 29}[args.dtype]
+        args.log2n = 28 if args.workload == "quicksort" else \
+            {"u64": 30, "u32": 31, "kv": 29}[args.dtype]
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "quicksort":
+        run_quicksort(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -202,6 +202,27 @@ lp_status lp_quicksort_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t see
 lp_status lp_quicksort_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint64_t seed,
                            cudaStream_t stream);
 
+/* What the last lp_quicksort_* on ctx did.  Keys "streamed" are read once and
+ * written once by a kernel: the algorithmic traffic is 2 x key bytes x keys.
+ * The times are device times (CUDA events) and are set only when timing is on
+ * (lp_ctx_set_timing); timing adds one stream synchronisation per level. */
+typedef struct {
+  uint32_t levels;          /* partition levels (each one batched launch or more) */
+  uint32_t timed;           /* 1 if the two times below were measured */
+  uint64_t partition_keys;  /* keys streamed by the batched partitions, all levels */
+  uint64_t sort_keys;       /* keys sorted in shared memory */
+  float partition_ms;       /* device time of the partition levels */
+  float sort_ms;            /* device time of the shared-memory sorts */
+} lp_sort_stats;
+lp_status lp_ctx_sort_stats(const lp_ctx *ctx, lp_sort_stats *out);
+
+/* Keys streamed (summed over every level of every segment, plus the segments
+ * finished in shared memory) by the last lp_partition_batched_u64 on ctx, or by
+ * the last launch of `batch`.  Both synchronise: the first the stream of the
+ * batched call, the second `stream`, which must be the stream of that launch. */
+lp_status lp_ctx_last_batch_keys(lp_ctx *ctx, uint64_t *keys_out);
+lp_status lp_batch_streamed_keys(lp_batch *batch, cudaStream_t stream, uint64_t *keys_out);
+
 /* ------------------------------------------ Blocked-Prefix-Sum partition
  * The low-space partition of Sec. 3 with explicit block size: count the
  * predecessors (swapping the roles on the reversed array when they are the

@@ -43,6 +43,11 @@ class lp_batch_tuning(C.Structure):
                 ("group_workers", C.c_uint32)]
 
 
+class lp_sort_stats(C.Structure):
+    _fields_ = [("levels", C.c_uint32), ("timed", C.c_uint32), ("partition_keys", C.c_uint64),
+                ("sort_keys", C.c_uint64), ("partition_ms", C.c_float), ("sort_ms", C.c_float)]
+
+
 _SIGS = {
     "lp_ctx_create": (_i, [C.POINTER(_p), _i]),
     "lp_ctx_destroy": (_i, [_p]),
@@ -74,6 +79,9 @@ _SIGS = {
     "lp_ctx_set_batch_tuning": (_i, [_p, _p]),
     "lp_quicksort_u64": (_i, [_p, _p, _u64, _u64, _p]),
     "lp_quicksort_u32": (_i, [_p, _p, _u64, _u64, _p]),
+    "lp_ctx_sort_stats": (_i, [_p, _p]),
+    "lp_ctx_last_batch_keys": (_i, [_p, _pu64]),
+    "lp_batch_streamed_keys": (_i, [_p, _p, _pu64]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -155,6 +163,18 @@ class Ctx:
     @property
     def aux_bytes(self):
         return int(lib().lp_ctx_aux_bytes(self.h))
+
+    def sort_stats(self):
+        """lp_ctx_sort_stats: what the last quicksort on this context did."""
+        st = lp_sort_stats()
+        self.check(lib().lp_ctx_sort_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in lp_sort_stats._fields_}
+
+    def last_batch_keys(self):
+        """lp_ctx_last_batch_keys: keys streamed by the last one-shot batch."""
+        k = C.c_uint64()
+        self.check(lib().lp_ctx_last_batch_keys(self.h, C.byref(k)))
+        return int(k.value)
 
     @property
     def last_launches(self):
@@ -283,6 +303,12 @@ class Batch:
 
     def launch(self, stream=None):
         self.ctx.check(lib().lp_batch_launch(self.h, _stream(stream)))
+
+    def streamed_keys(self, stream=None):
+        """lp_batch_streamed_keys: keys streamed by the last launch."""
+        k = C.c_uint64()
+        self.ctx.check(lib().lp_batch_streamed_keys(self.h, _stream(stream), C.byref(k)))
+        return int(k.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -82,6 +82,7 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
   if (!c) return LP_ERR_INVALID_ARG;
   c->err.clear();
   c->last_launches = 0;
+  c->last_batch_traffic = nullptr;
   if (count && !d_splits) return lp_fail(c, LP_ERR_INVALID_ARG, "null d_splits");
   lp_status st = check_segments(c, segs, count);
   if (st != LP_OK) return st;
@@ -124,6 +125,7 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
   c->last_stream = stream;
   e = lp::launch_batched<uint64_t>(reinterpret_cast<lp::SegDesc*>(c->d_batch), count, seed,
                                    d_splits, B, tune, cfg);
+  c->last_batch_traffic = B.totals + 2;
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "launch");
   return LP_OK;
@@ -195,7 +197,7 @@ lp_status lp_batch_launch(lp_batch* b, cudaStream_t stream) {
   cudaError_t e = cudaSetDevice(b->ctx->device);
   if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, stream);
   if (e != cudaSuccess) return lp_cuda_fail(b->ctx, e, "graph launch");
-  b->ctx->last_launches = 3;  // set-up kernel, two resets, persistent kernel (one graph)
+  b->ctx->last_launches = 2;  // kernels of the graph: set-up and the persistent kernel
   return LP_OK;
 }
 
@@ -295,10 +297,23 @@ lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, cudaStre
   lp::LaunchCfg cfg{tuned_grid(c, tune, sizeof(T)), stream, 0, nullptr};
   c->last_timed = false;
   c->last_stream = stream;
+  c->sort_stats = lp_sort_stats{};
+  if (c->timing && !c->events_made) {
+    for (int i = 0; i < 2; i++)
+      if ((e = cudaEventCreate(&c->ev[i])) != cudaSuccess) return lp_cuda_fail(c, e, "events");
+    c->events_made = true;
+  }
+  lp::SortStats ss{};
   e = lp::launch_quicksort<T>(keys, n, seed, c->d_var, c->h_pinned, tune, c->task.bar,
-                              c->task.status, cfg, nullptr);
+                              c->task.status, cfg, c->timing ? c->ev : nullptr, &ss);
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "quicksort");
+  c->sort_stats.levels = ss.levels;
+  c->sort_stats.timed = c->timing ? 1u : 0u;
+  c->sort_stats.partition_keys = ss.partition_keys;
+  c->sort_stats.sort_keys = ss.sort_keys;
+  c->sort_stats.partition_ms = ss.partition_ms;
+  c->sort_stats.sort_ms = ss.sort_ms;
   e = cudaMemcpyAsync(c->h_pinned, c->task.status, 4, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "read status");
@@ -311,6 +326,40 @@ lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, cudaStre
 }  // namespace
 
 extern "C" {
+
+lp_status lp_ctx_sort_stats(const lp_ctx* c, lp_sort_stats* out) {
+  if (!c || !out) return LP_ERR_INVALID_ARG;
+  *out = c->sort_stats;
+  return LP_OK;
+}
+
+lp_status lp_ctx_last_batch_keys(lp_ctx* c, uint64_t* keys_out) {
+  if (!c || !keys_out) return LP_ERR_INVALID_ARG;
+  *keys_out = 0;
+  if (!c->last_batch_traffic) return LP_OK;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_pinned, c->last_batch_traffic, 8, cudaMemcpyDeviceToHost,
+                        c->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "read streamed keys");
+  *keys_out = c->h_pinned[0];
+  return LP_OK;
+}
+
+lp_status lp_batch_streamed_keys(lp_batch* b, cudaStream_t stream, uint64_t* keys_out) {
+  if (!b || !keys_out) return LP_ERR_INVALID_ARG;
+  *keys_out = 0;
+  if (b->count == 0) return LP_OK;
+  lp_ctx* c = b->ctx;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_pinned, b->B.totals + 2, 8, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "read streamed keys");
+  *keys_out = c->h_pinned[0];
+  return LP_OK;
+}
 
 lp_status lp_quicksort_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,
                            cudaStream_t stream) {

@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
             } else if ((level == 0 && n <= cta_cap) || (level > 0 && m <= cta_cap)) {
               d.state = kSegCta;
               gc = 1;
+              atomicAdd(&B.totals[2], (unsigned long long)(level == 0 ? n : m));
             } else {
+              atomicAdd(&B.totals[2], (unsigned long long)m);
               const StepParams P =
                   choose_params(m, R::K, a.group_workers, a.line_bytes, a.min_chunks);
               d.b = P.b;
@@ -276,8 +278,10 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
 
 // Per-segment set-up on the device: the 16-byte aligned body of each segment.
 template <typename T>
-__global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed) {
+__global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed,
+                                   unsigned long long* traffic) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *traffic = 0ull;
   if (s >= count) return;
   SegDesc& d = segs[s];
   constexpr uint32_t K = sizeof(T), A = 16 / sizeof(T);
@@ -326,7 +330,8 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   using R = Tr<T, false>;
   cudaStream_t st = cfg.stream;
   if (count == 0) return cudaSuccess;
-  batch_setup_kernel<T><<<(count + 255) / 256, 256, 0, st>>>(d_segs, count, seed);
+  batch_setup_kernel<T><<<(count + 255) / 256, 256, 0, st>>>(d_segs, count, seed,
+                                                              Bs.totals + 2);
   cfg.launches++;
   cudaError_t e = cudaMemsetAsync(Bs.bar, 0, 8, st);
   if (e != cudaSuccess) return e;

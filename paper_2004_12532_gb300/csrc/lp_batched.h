@@ -37,7 +37,7 @@ struct BatchArgs {
 struct BatchScratch {
   unsigned long long* wprefix;  // count + 1 task prefix entries
   uint32_t* ctalist;            // count CTA-task segment ids
-  unsigned long long* totals;   // warp tasks, CTA tasks of the round
+  unsigned long long* totals;   // warp tasks, CTA tasks of the round; keys streamed
   uint32_t* counters;           // task fetch counters
   uint32_t* bar;                // grid barrier
   uint32_t* status;
@@ -63,14 +63,22 @@ template <typename T>
 cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
                            const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg);
 
-// Quicksort on the batched partition (lp_quicksort.cu).  `host_words`: 16
+// Quicksort on the batched partition (lp_quicksort.cu).  `host_words`: 32
 // bytes of pinned host memory for list sizes; synchronises `cfg.stream` once
-// or twice per level.
+// or twice per level.  `ev` (two events, or null) times the partition levels
+// and the shared-memory sorts.
+struct SortStats {
+  uint32_t levels;
+  uint64_t partition_keys;  // keys streamed by the batched partitions (all levels)
+  uint64_t sort_keys;       // keys sorted in shared memory
+  float partition_ms, sort_ms;
+};
+
 size_t quicksort_scratch_bytes(uint64_t n);
 
 template <typename T>
 cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* host_words,
                              const BatchTuning& tune, uint32_t* bar, uint32_t* status,
-                             LaunchCfg& cfg, uint32_t* levels_out);
+                             LaunchCfg& cfg, const cudaEvent_t* ev, SortStats* stats);
 
 }  // namespace lp

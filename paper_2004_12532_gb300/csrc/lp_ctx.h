@@ -34,6 +34,8 @@ struct lp_ctx {
   void* h_batch = nullptr;
   size_t h_batch_bytes = 0;
   lp_batch_tuning tuning{0, 0, 0, 0};
+  unsigned long long* last_batch_traffic = nullptr;  // streamed-keys counter of the last batch
+  lp_sort_stats sort_stats{};                         // of the last quicksort
 };
 
 

@@ -40,9 +40,10 @@ struct QsEq {
   uint64_t lo, n, pivot;
 };
 
-// list sizes, in device memory
+// list sizes of the level and keys streamed, in device memory
 struct QsCounts {
-  uint32_t next, small, eq, pad;
+  uint32_t next, small, eq, pad;           // reset every level
+  unsigned long long part_keys, sort_keys; // whole call
 };
 
 template <typename T>
@@ -89,15 +90,25 @@ __global__ void qs_build_eq_kernel(const QsEq* list, uint32_t count, T* keys, Se
 __device__ __forceinline__ void qs_push(QsSeg* next, QsSeg* small, QsCounts* c, uint64_t lo,
                                         uint64_t n) {
   if (n <= 1) return;  // a single key is in place
-  if (n <= kCut) small[atomicAdd(&c->small, 1u)] = QsSeg{lo, n};
-  else next[atomicAdd(&c->next, 1u)] = QsSeg{lo, n};
+  if (n <= kCut) {
+    small[atomicAdd(&c->small, 1u)] = QsSeg{lo, n};
+    atomicAdd(&c->sort_keys, (unsigned long long)n);
+  } else {
+    next[atomicAdd(&c->next, 1u)] = QsSeg{lo, n};
+  }
+}
+
+// keys the batched launch just before streamed, added to the call's total
+__device__ __forceinline__ void qs_add_traffic(QsCounts* c, const unsigned long long* traffic) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->part_keys += *traffic;
 }
 
 // Children of each partitioned subarray.  A subarray with no successor goes
 // to the equal-key list unless its pivot is 0 (then every key is 0).
 __global__ void qs_split_kernel(const QsSeg* list, uint32_t count, const SegDesc* segs,
                                 const uint64_t* splits, QsSeg* next, QsSeg* small, QsEq* eq,
-                                QsCounts* c) {
+                                QsCounts* c, const unsigned long long* traffic) {
+  qs_add_traffic(c, traffic);
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= count) return;
   const QsSeg q = list[s];
@@ -113,7 +124,9 @@ __global__ void qs_split_kernel(const QsSeg* list, uint32_t count, const SegDesc
 
 // After the pass by [x < pivot]: [lo, lo + t') stays open, the rest is final.
 __global__ void qs_split_eq_kernel(const QsEq* eq, uint32_t count, const uint64_t* splits,
-                                   QsSeg* next, QsSeg* small, QsCounts* c) {
+                                   QsSeg* next, QsSeg* small, QsCounts* c,
+                                   const unsigned long long* traffic) {
+  qs_add_traffic(c, traffic);
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= count) return;
   qs_push(next, small, c, eq[s].lo, splits[s]);
@@ -203,9 +216,9 @@ size_t quicksort_scratch_bytes(uint64_t n) { return qs_layout(nullptr, n).bytes;
 template <typename T>
 cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* host_words,
                              const BatchTuning& tune, uint32_t* bar, uint32_t* status,
-                             LaunchCfg& cfg, uint32_t* levels_out) {
+                             LaunchCfg& cfg, const cudaEvent_t* ev, SortStats* stats) {
   cudaStream_t st = cfg.stream;
-  if (levels_out) *levels_out = 0;
+  *stats = SortStats{};
   if (n < 2) return cudaSuccess;
   const QsLayout L = qs_layout(scratch, n);
   const BatchScratch Bs = carve_batch_scratch(L.batch, L.slice, bar, status);
@@ -213,6 +226,8 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
   cudaError_t e;
   uint64_t open = 0;
   uint32_t nsmall = 0, cur = 0, levels = 0;
+  e = cudaMemsetAsync(L.counts, 0, sizeof(QsCounts), st);
+  if (e != cudaSuccess) return e;
   {
     const QsSeg whole{0, n};
     // the whole array is the first open subarray, or the only small one
@@ -221,18 +236,35 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
     if (e != cudaSuccess) return e;
     if (n > kCut) open = 1; else nsmall = 1;
   }
+  // optional timing: events around a stretch of launches, read after the
+  // host's next synchronisation of the stream
+  auto mark = [&](int k) -> cudaError_t { return ev ? cudaEventRecord(ev[k], st) : cudaSuccess; };
+  auto elapsed = [&](float* acc) {
+    float ms = 0.f;
+    if (ev && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) *acc += ms;
+  };
   auto sort_small = [&](uint32_t cnt) -> cudaError_t {
     if (cnt == 0) return cudaSuccess;
     const uint32_t grid = cnt < 8192 ? cnt : 8192;
+    cudaError_t r = mark(0);
+    if (r != cudaSuccess) return r;
     qs_small_sort_kernel<T><<<grid, kSortThreads, 0, st>>>(L.small, cnt, keys);
     cfg.launches++;
-    return cudaGetLastError();
+    if ((r = cudaGetLastError()) != cudaSuccess) return r;
+    if (ev) {
+      if ((r = mark(1)) != cudaSuccess || (r = cudaEventSynchronize(ev[1])) != cudaSuccess)
+        return r;
+      elapsed(&stats->sort_ms);
+    }
+    return cudaSuccess;
   };
+  const unsigned long long* traffic = Bs.totals + 2;
   while (open > 0) {
     if (++levels > kMaxSortLevels) return cudaErrorUnknown;  // sizes shrink every level
     QsSeg* list = L.lists[cur];
     QsSeg* next = L.lists[cur ^ 1];
-    e = cudaMemsetAsync(L.counts, 0, sizeof(QsCounts), st);
+    e = cudaMemsetAsync(L.counts, 0, 16, st);  // the level's list sizes
+    if (e == cudaSuccess) e = mark(0);
     if (e != cudaSuccess) return e;
     for (uint64_t o = 0; o < open; o += L.slice) {
       const uint32_t cnt = (uint32_t)(open - o < L.slice ? open - o : L.slice);
@@ -242,11 +274,14 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
       e = launch_batched<T>(L.segs, cnt, sm_stream(seed, levels), L.splits, Bs, tune, cfg);
       if (e != cudaSuccess) return e;
       qs_split_kernel<<<blocks, 256, 0, st>>>(list + o, cnt, L.segs, L.splits, next, L.small,
-                                              L.eq, L.counts);
+                                              L.eq, L.counts, traffic);
       cfg.launches++;
     }
+    if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = read_counts(L, hc, st)) != cudaSuccess) return e;
+    elapsed(&stats->partition_ms);
     const uint32_t neq = hc->eq;
+    if (neq > 0 && (e = mark(0)) != cudaSuccess) return e;
     for (uint32_t o = 0; o < neq; o += L.slice) {  // split off the keys equal to the pivot
       const uint32_t cnt = neq - o < L.slice ? neq - o : L.slice;
       const unsigned blocks = (cnt + 255) / 256;
@@ -255,24 +290,31 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
       e = launch_batched<T>(L.segs, cnt, sm_stream(~seed, levels), L.splits, Bs, tune, cfg);
       if (e != cudaSuccess) return e;
       qs_split_eq_kernel<<<blocks, 256, 0, st>>>(L.eq + o, cnt, L.splits, next, L.small,
-                                                 L.counts);
+                                                 L.counts, traffic);
       cfg.launches++;
     }
-    if (neq > 0 && (e = read_counts(L, hc, st)) != cudaSuccess) return e;
+    if (neq > 0) {
+      if ((e = mark(1)) != cudaSuccess) return e;
+      if ((e = read_counts(L, hc, st)) != cudaSuccess) return e;
+      elapsed(&stats->partition_ms);
+    }
     if ((e = sort_small(hc->small)) != cudaSuccess) return e;
     open = hc->next;
     cur ^= 1;
   }
   if ((e = sort_small(nsmall)) != cudaSuccess) return e;
-  if (levels_out) *levels_out = levels;
+  if ((e = read_counts(L, hc, st)) != cudaSuccess) return e;
+  stats->levels = levels;
+  stats->partition_keys = hc->part_keys;
+  stats->sort_keys = hc->sort_keys + (n <= kCut ? n : 0);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_quicksort<uint64_t>(uint64_t*, uint64_t, uint64_t, void*, void*,
                                                 const BatchTuning&, uint32_t*, uint32_t*,
-                                                LaunchCfg&, uint32_t*);
+                                                LaunchCfg&, const cudaEvent_t*, SortStats*);
 template cudaError_t launch_quicksort<uint32_t>(uint32_t*, uint64_t, uint64_t, void*, void*,
                                                 const BatchTuning&, uint32_t*, uint32_t*,
-                                                LaunchCfg&, uint32_t*);
+                                                LaunchCfg&, const cudaEvent_t*, SortStats*);
 
 }  // namespace lp
