@@ -223,6 +223,99 @@ lp_status lp_ctx_sort_stats(const lp_ctx *ctx, lp_sort_stats *out);
 lp_status lp_ctx_last_batch_keys(lp_ctx *ctx, uint64_t *keys_out);
 lp_status lp_batch_streamed_keys(lp_batch *batch, cudaStream_t stream, uint64_t *keys_out);
 
+/* ------------------------------------------------------------ serving
+ * A request engine (no counterpart in the paper): partition and sort requests
+ * of mixed sizes and key widths are admitted first-in first-out while a slot
+ * is free and the device-memory budget holds their keys (plus, for a sort, its
+ * level lists), and are run by continuous batching.  Every engine step is one
+ * batched launch per key width holding the newly admitted partitions and the
+ * current quicksort level of every sort in flight, then the children split and
+ * the shared-memory sorts of all those sorts; requests that arrive meanwhile
+ * join the next step.  A partition finishes in the step it joins, a sort after
+ * as many steps as its quicksort has levels.  Each result is the same whatever
+ * the request was batched with (a partition's offsets X follow from the engine
+ * seed and the request seed only; a sort's result is the sorted array).
+ *
+ * Keys live in one device allocation of budget_bytes made at creation (the
+ * arena); a request's keys are generated on the device from its seed (uniform
+ * keys, as lp_fill_uniform_*), or copied from d_src, when it is admitted.  The
+ * server owns an lp_ctx and a stream of its own; calls on one server must come
+ * from one thread.  lp_server_step runs one engine step and synchronises. */
+typedef struct lp_server lp_server;
+
+typedef struct {
+  uint64_t budget_bytes;  /* device memory for request keys and sort lists */
+  uint32_t max_slots;     /* requests admitted at once, at most (0: 256) */
+  uint32_t max_segments;  /* segment records per key width per step (0: 65536) */
+  uint64_t seed;          /* seeds the offsets X of every batched launch */
+  uint32_t keep_results;  /* 1: finished requests keep their keys until lp_server_release */
+  uint32_t pad;
+} lp_server_config;
+
+enum { LP_REQ_PARTITION = 0, LP_REQ_SORT = 1 };
+enum { LP_SERVE_CONTINUOUS = 0, LP_SERVE_ONE_AT_A_TIME = 1 };
+
+typedef struct {
+  uint32_t kind;       /* LP_REQ_PARTITION or LP_REQ_SORT */
+  uint32_t key_bits;   /* 32 or 64 */
+  uint64_t n;
+  uint64_t pivot;      /* partition: dec(x) = [x <= pivot] */
+  uint64_t seed;       /* names the request; the keys' generator seed when d_src is NULL */
+  const void *d_src;   /* device keys copied in on admission (keep them unchanged until
+                          the request is admitted), or NULL */
+  double arrival_s;    /* server clock (lp_server_now); in lp_server_run: since the run began */
+} lp_request;
+
+typedef struct {
+  uint64_t id;
+  uint32_t kind, key_bits;
+  uint64_t n;
+  uint64_t split;      /* partition: keys <= pivot */
+  double arrival_s, admit_s, done_s;  /* server clock */
+  uint32_t steps;      /* engine steps the request took part in */
+  uint32_t pad;
+} lp_completion;
+
+typedef struct {
+  uint64_t steps, launches, completed, keys_done;
+  uint64_t peak_bytes;    /* arena bytes in use, at most */
+  uint64_t budget_bytes, in_use_bytes, engine_bytes;
+  double busy_s;          /* host time spent in engine steps */
+} lp_server_stats;
+
+/* Errors: LP_ERR_INVALID_ARG (bad config), LP_ERR_OOM (the budget or the
+ * engine's ~20 MB of tables cannot be allocated), LP_ERR_CUDA. */
+lp_status lp_server_create(int device, const lp_server_config *cfg, lp_server **out);
+lp_status lp_server_destroy(lp_server *server);
+const char *lp_server_last_error(const lp_server *server);
+double lp_server_now(const lp_server *server);
+/* Queues a request (host only).  LP_ERR_INVALID_ARG: bad kind or width, a
+ * request larger than the budget, or a sort with more than max_segments *
+ * 4097 keys. */
+lp_status lp_server_submit(lp_server *server, const lp_request *req, uint64_t *id_out);
+/* Admits what fits, runs one engine step, synchronises; *in_flight_out =
+ * requests admitted and not finished.  After a device error the server
+ * refuses further steps (LP_ERR_TIMEOUT / LP_ERR_CUDA). */
+lp_status lp_server_step(lp_server *server, uint32_t *in_flight_out);
+/* Moves up to cap finished requests' records to out, oldest first. */
+lp_status lp_server_poll(lp_server *server, lp_completion *out, uint32_t cap, uint32_t *got);
+/* keep_results: device address of a finished request's keys; fetch copies
+ * the first `bytes` of them to dst (host or device memory, synchronous);
+ * release frees them. */
+lp_status lp_server_result(lp_server *server, uint64_t id, void **d_keys_out);
+lp_status lp_server_fetch(lp_server *server, uint64_t id, void *dst, uint64_t bytes);
+lp_status lp_server_release(lp_server *server, uint64_t id);
+lp_status lp_server_get_stats(const lp_server *server, lp_server_stats *out);
+/* Keys streamed by all batched launches of the engine (read once, written once). */
+lp_status lp_server_streamed_keys(lp_server *server, uint64_t *keys_out);
+/* Open-loop driver: submits reqs[i] at arrival_s seconds after the call
+ * begins (arrivals in time order), steps the engine until every request is
+ * done and writes request i's record to out[i].  LP_SERVE_ONE_AT_A_TIME runs
+ * the same requests one at a time in arrival order through lp_partition_* and
+ * lp_quicksort_* instead (the per-request baseline). */
+lp_status lp_server_run(lp_server *server, const lp_request *reqs, uint32_t count,
+                        uint32_t mode, lp_completion *out);
+
 /* ------------------------------------------ Blocked-Prefix-Sum partition
  * The low-space partition of Sec. 3 with explicit block size: count the
  * predecessors (swapping the roles on the reversed array when they are the

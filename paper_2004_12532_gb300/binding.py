@@ -48,6 +48,32 @@ class lp_sort_stats(C.Structure):
                 ("sort_keys", C.c_uint64), ("partition_ms", C.c_float), ("sort_ms", C.c_float)]
 
 
+class lp_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("max_slots", C.c_uint32),
+                ("max_segments", C.c_uint32), ("seed", C.c_uint64),
+                ("keep_results", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class lp_request(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("key_bits", C.c_uint32), ("n", C.c_uint64),
+                ("pivot", C.c_uint64), ("seed", C.c_uint64), ("d_src", C.c_void_p),
+                ("arrival_s", C.c_double)]
+
+
+class lp_completion(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("kind", C.c_uint32), ("key_bits", C.c_uint32),
+                ("n", C.c_uint64), ("split", C.c_uint64), ("arrival_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double), ("steps", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
+class lp_server_stats(C.Structure):
+    _fields_ = [("steps", C.c_uint64), ("launches", C.c_uint64), ("completed", C.c_uint64),
+                ("keys_done", C.c_uint64), ("peak_bytes", C.c_uint64),
+                ("budget_bytes", C.c_uint64), ("in_use_bytes", C.c_uint64),
+                ("engine_bytes", C.c_uint64), ("busy_s", C.c_double)]
+
+
 _SIGS = {
     "lp_ctx_create": (_i, [C.POINTER(_p), _i]),
     "lp_ctx_destroy": (_i, [_p]),
@@ -82,6 +108,19 @@ _SIGS = {
     "lp_ctx_sort_stats": (_i, [_p, _p]),
     "lp_ctx_last_batch_keys": (_i, [_p, _pu64]),
     "lp_batch_streamed_keys": (_i, [_p, _p, _pu64]),
+    "lp_server_create": (_i, [_i, _p, C.POINTER(_p)]),
+    "lp_server_destroy": (_i, [_p]),
+    "lp_server_last_error": (C.c_char_p, [_p]),
+    "lp_server_now": (C.c_double, [_p]),
+    "lp_server_submit": (_i, [_p, _p, _pu64]),
+    "lp_server_step": (_i, [_p, C.POINTER(_u32)]),
+    "lp_server_poll": (_i, [_p, _p, _u32, C.POINTER(_u32)]),
+    "lp_server_result": (_i, [_p, _u64, C.POINTER(_p)]),
+    "lp_server_fetch": (_i, [_p, _u64, _p, _u64]),
+    "lp_server_release": (_i, [_p, _u64]),
+    "lp_server_get_stats": (_i, [_p, _p]),
+    "lp_server_streamed_keys": (_i, [_p, _pu64]),
+    "lp_server_run": (_i, [_p, _p, _u32, _u32, _p]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -385,3 +424,114 @@ def lp_fill_iota_u64(vals, stream=None):
     st = lib().lp_fill_iota_u64(p, n, _stream(stream))
     if st != LP_OK:
         raise LPError(st, "lp_fill_iota_u64")
+
+
+# ---------------------------------------------------------------- serving
+
+LP_REQ_PARTITION = 0
+LP_REQ_SORT = 1
+LP_SERVE_CONTINUOUS = 0
+LP_SERVE_ONE_AT_A_TIME = 1
+
+
+def _completion_dict(c):
+    return {f: getattr(c, f) for f, _ in lp_completion._fields_ if f != "pad"}
+
+
+class Server:
+    """lp_server: continuous-batching engine for partition and sort requests."""
+
+    def __init__(self, device=None, budget_bytes=1 << 30, max_slots=0, max_segments=0, seed=1,
+                 keep_results=False):
+        if device is None:
+            device = torch.cuda.current_device()
+        cfg = lp_server_config(int(budget_bytes), int(max_slots), int(max_segments), int(seed),
+                               1 if keep_results else 0, 0)
+        h = C.c_void_p()
+        st = lib().lp_server_create(int(device), C.byref(cfg), C.byref(h))
+        if st != LP_OK:
+            raise LPError(st, "lp_server_create")
+        self.h = h
+
+    def check(self, st):
+        if st != LP_OK:
+            raise LPError(st, lib().lp_server_last_error(self.h).decode())
+        return st
+
+    @staticmethod
+    def request(kind, key_bits, n, pivot=0, seed=0, src=None, arrival_s=0.0):
+        r = lp_request()
+        r.kind, r.key_bits, r.n, r.pivot, r.seed = int(kind), int(key_bits), int(n), \
+            int(pivot), int(seed)
+        if src is not None:
+            p, m = _dev_ptr(src, int(key_bits))
+            if m != n:
+                raise ValueError("src length differs from n")
+            r.d_src = p.value
+        r.arrival_s = float(arrival_s)
+        return r
+
+    def now(self):
+        return float(lib().lp_server_now(self.h))
+
+    def submit(self, kind, key_bits, n, pivot=0, seed=0, src=None, arrival_s=None):
+        r = self.request(kind, key_bits, n, pivot, seed, src,
+                         self.now() if arrival_s is None else arrival_s)
+        i = C.c_uint64()
+        self.check(lib().lp_server_submit(self.h, C.byref(r), C.byref(i)))
+        return int(i.value)
+
+    def step(self):
+        k = C.c_uint32()
+        self.check(lib().lp_server_step(self.h, C.byref(k)))
+        return int(k.value)
+
+    def poll(self, cap=1024):
+        buf = (lp_completion * cap)()
+        got = C.c_uint32()
+        self.check(lib().lp_server_poll(self.h, buf, cap, C.byref(got)))
+        return [_completion_dict(buf[i]) for i in range(got.value)]
+
+    def result_ptr(self, id_):
+        p = C.c_void_p()
+        self.check(lib().lp_server_result(self.h, int(id_), C.byref(p)))
+        return int(p.value)
+
+    def fetch(self, id_, n, key_bits):
+        """The finished request's keys as a numpy array (keep_results)."""
+        import numpy as np
+        out = np.empty(int(n), dtype=np.uint64 if key_bits == 64 else np.uint32)
+        self.check(lib().lp_server_fetch(self.h, int(id_), C.c_void_p(out.ctypes.data),
+                                         out.nbytes))
+        return out
+
+    def release(self, id_):
+        self.check(lib().lp_server_release(self.h, int(id_)))
+
+    def stats(self):
+        st = lp_server_stats()
+        self.check(lib().lp_server_get_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in lp_server_stats._fields_}
+
+    def streamed_keys(self):
+        k = C.c_uint64()
+        self.check(lib().lp_server_streamed_keys(self.h, C.byref(k)))
+        return int(k.value)
+
+    def run(self, requests, mode=LP_SERVE_CONTINUOUS):
+        """Open-loop run of lp_request records (arrival_s relative to the start)."""
+        arr = (lp_request * len(requests))(*requests)
+        out = (lp_completion * len(requests))()
+        self.check(lib().lp_server_run(self.h, arr, len(requests), int(mode), out))
+        return [_completion_dict(out[i]) for i in range(len(requests))]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

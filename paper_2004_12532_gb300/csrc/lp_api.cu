@@ -76,6 +76,22 @@ lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream) {
   return LP_OK;
 }
 
+// Creates the context's timing events once.
+lp_status ensure_events(lp_ctx* c) {
+  if (c->events_made) return LP_OK;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  for (int i = 0; i < 3; i++) {
+    e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < i; j++) cudaEventDestroy(c->ev[j]);
+      return cuda_fail(c, e, "cudaEventCreate");
+    }
+  }
+  c->events_made = true;
+  return LP_OK;
+}
+
 namespace {
 
 constexpr uint64_t kLowspaceBlock = 4096;  // B of the low-space partition (Sec. 5)
@@ -271,7 +287,7 @@ lp_status lp_ctx_destroy(lp_ctx* c) {
   if (!c) return LP_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   if (c->events_made)
-    for (int i = 0; i < 2; i++) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < 3; i++) cudaEventDestroy(c->ev[i]);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_var) cudaFree(c->d_var);
   if (c->d_batch) cudaFree(c->d_batch);
@@ -288,14 +304,9 @@ uint32_t lp_ctx_grid(const lp_ctx* c) { return c ? c->grid_u64 : 0; }
 
 lp_status lp_ctx_set_timing(lp_ctx* c, int enable) {
   if (!c) return LP_ERR_INVALID_ARG;
-  if (enable && !c->events_made) {
-    cudaError_t e = cudaSetDevice(c->device);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    for (int i = 0; i < 2; i++) {
-      e = cudaEventCreate(&c->ev[i]);
-      if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
-    }
-    c->events_made = true;
+  if (enable) {
+    lp_status s = ensure_events(c);
+    if (s != LP_OK) return s;
   }
   c->timing = enable != 0;
   return LP_OK;

@@ -59,6 +59,18 @@ size_t records_bytes(uint32_t count) {
   return ((size_t)count * sizeof(lp::SegDesc) + 255) / 256 * 256;
 }
 
+// Grows the pinned staging buffer of the context to at least `bytes`.
+lp_status ensure_staging(lp_ctx* c, size_t bytes) {
+  if (bytes <= c->h_batch_bytes) return LP_OK;
+  if (c->h_batch) cudaFreeHost(c->h_batch);
+  c->h_batch = nullptr;
+  c->h_batch_bytes = 0;
+  if (cudaMallocHost(&c->h_batch, bytes) != cudaSuccess)
+    return lp_fail(c, LP_ERR_OOM, "pinned staging allocation failed");
+  c->h_batch_bytes = bytes;
+  return LP_OK;
+}
+
 // CTAs of a batched launch: the tuned count, at most every resident CTA
 uint32_t tuned_grid(const lp_ctx* c, const lp::BatchTuning& t, size_t key_bytes) {
   const uint32_t full = key_bytes == 8 ? c->grid_batch_u64 : c->grid_batch_u32;
@@ -103,14 +115,7 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
     c->batch_bytes = need;
     c->aux_bytes = c->scratch_bytes + c->var_bytes + c->batch_bytes;
   }
-  if (rec > c->h_batch_bytes) {
-    if (c->h_batch) cudaFreeHost(c->h_batch);
-    c->h_batch = nullptr;
-    c->h_batch_bytes = 0;
-    if (cudaMallocHost(&c->h_batch, rec) != cudaSuccess)
-      return lp_fail(c, LP_ERR_OOM, "pinned staging allocation failed");
-    c->h_batch_bytes = rec;
-  }
+  if ((st = ensure_staging(c, rec)) != LP_OK) return st;
   std::vector<lp::SegDesc> recs;
   fill_records(recs, segs, count);
   memcpy(c->h_batch, recs.data(), (size_t)count * sizeof(lp::SegDesc));
@@ -298,13 +303,10 @@ lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, cudaStre
   c->last_timed = false;
   c->last_stream = stream;
   c->sort_stats = lp_sort_stats{};
-  if (c->timing && !c->events_made) {
-    for (int i = 0; i < 2; i++)
-      if ((e = cudaEventCreate(&c->ev[i])) != cudaSuccess) return lp_cuda_fail(c, e, "events");
-    c->events_made = true;
-  }
+  if (c->timing && (ls = ensure_events(c)) != LP_OK) return ls;
+  if ((ls = ensure_staging(c, lp::quicksort_staging_bytes(n))) != LP_OK) return ls;
   lp::SortStats ss{};
-  e = lp::launch_quicksort<T>(keys, n, seed, c->d_var, c->h_pinned, tune, c->task.bar,
+  e = lp::launch_quicksort<T>(keys, n, seed, c->d_var, c->h_batch, tune, c->task.bar,
                               c->task.status, cfg, c->timing ? c->ev : nullptr, &ss);
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "quicksort");

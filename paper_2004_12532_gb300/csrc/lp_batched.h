@@ -63,10 +63,11 @@ template <typename T>
 cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
                            const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg);
 
-// Quicksort on the batched partition (lp_quicksort.cu).  `host_words`: 32
-// bytes of pinned host memory for list sizes; synchronises `cfg.stream` once
-// or twice per level.  `ev` (two events, or null) times the partition levels
-// and the shared-memory sorts.
+// Quicksort on the batched partition (lp_quicksort.cu).  `staging`:
+// quicksort_staging_bytes(n) of pinned host memory for the per-level job
+// records and read-backs; synchronises `cfg.stream` once per level.  `ev`
+// (three events, or null) times the partition levels and the shared-memory
+// sorts.
 struct SortStats {
   uint32_t levels;
   uint64_t partition_keys;  // keys streamed by the batched partitions (all levels)
@@ -75,9 +76,10 @@ struct SortStats {
 };
 
 size_t quicksort_scratch_bytes(uint64_t n);
+size_t quicksort_staging_bytes(uint64_t n);
 
 template <typename T>
-cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* host_words,
+cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* staging,
                              const BatchTuning& tune, uint32_t* bar, uint32_t* status,
                              LaunchCfg& cfg, const cudaEvent_t* ev, SortStats* stats);
 

@@ -23,7 +23,7 @@ struct lp_ctx {
   bool timing = false;
   bool events_made = false;
   bool last_timed = false;
-  cudaEvent_t ev[2];             // around the partition kernel of a timed call
+  cudaEvent_t ev[3];             // around the kernels of a timed call
   cudaStream_t last_stream = nullptr;
   void* d_var = nullptr;         // per-call scratch of the low-space partition (grown)
   size_t var_bytes = 0;
@@ -42,3 +42,4 @@ struct lp_ctx {
 lp_status lp_fail(lp_ctx* c, lp_status s, const char* what);
 lp_status lp_cuda_fail(lp_ctx* c, cudaError_t e, const char* where);
 lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream);
+lp_status ensure_events(lp_ctx* c);

@@ -1,189 +1,49 @@
-// lp_quicksort.cu -- quicksort on the partition (Sec. 5, "A Full Quicksort"):
-// the paper partitions in parallel at the top levels and serially once
-// subproblems are small.  On the GPU every level partitions all open
-// subarrays at once through the batched engine (lp_batched.cu), and
-// subarrays of at most kCut keys are sorted by one CTA each in shared memory.
+// lp_quicksort.cu -- quicksort of one array on the partition (Sec. 5, "A Full
+// Quicksort"): the paper partitions in parallel at the top levels and
+// serially once subproblems are small.  Here every level partitions all open
+// subarrays of the array at once through the batched engine (lp_batched.cu)
+// and the subarrays of at most kQsCut keys are sorted by one CTA each in
+// shared memory (kernels in lp_qs.cuh).
 //
-// Per level (device-resident lists; the host reads back the list sizes):
-//   build   pivot of each open subarray = median of three seeded samples;
-//   batch   partition every open subarray by [x <= pivot];
-//   split   children [lo, lo+t) and [lo+t, hi); a child of at most kCut keys
-//           goes to the level's small list; when every key was <= pivot
-//           (t = n), the subarray is partitioned again by [x < pivot]
-//           (pivot - 1) and only [lo, lo+t') stays open -- the keys equal to
-//           the pivot are in final place;
-//   sort    every subarray of the small list is sorted in shared memory.
-// Every open subarray holds more than kCut keys, so a level has at most
-// n / (kCut + 1) of them: the lists cost < 0.3% of the array's bytes (uint64).
-// The batched engine's per-segment records are used in slices of at most
-// kSlice segments, so they cost a fixed amount whatever n is.
+// Per level: build the segment records (median-of-3 pivots), one batched
+// launch per slice of at most kSlice subarrays, split into children, sort the
+// level's small subarrays, read the next list's size back (one host
+// synchronisation per level).  Auxiliary memory: two item lists of at most
+// n / (kQsCut + 1) items (32 bytes each), a small list of twice that (16
+// bytes each), and the records of one slice -- about 0.4% of a uint64 array's
+// bytes at n = 2^28, plus a fixed ~2.4 MB.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "lp_batched.h"
-#include "lp_device.cuh"
-#include "lp_launch.h"
-#include "lp_plan.h"
+#include "lp_qs.cuh"
 
 namespace lp {
 
 namespace {
 
-constexpr uint64_t kCut = 4096;     // subarrays this small are sorted in shared memory
 constexpr uint32_t kSlice = 16384;  // segments per batched launch, at most
 constexpr uint32_t kMaxSortLevels = 4096;
 
-struct QsSeg {
-  uint64_t lo, n;
-};
-struct QsEq {
-  uint64_t lo, n, pivot;
-};
-
-// list sizes of the level and keys streamed, in device memory
-struct QsCounts {
-  uint32_t next, small, eq, pad;           // reset every level
-  unsigned long long part_keys, sort_keys; // whole call
-};
-
-template <typename T>
-__device__ __forceinline__ T ldk(const T* p) {
-  if constexpr (sizeof(T) == 8) return (T)__ldcg(reinterpret_cast<const unsigned long long*>(p));
-  else return (T)__ldcg(reinterpret_cast<const unsigned int*>(p));
-}
-
-// Segment records of one slice of the open list: the pivot is the median of
-// three keys at seeded positions of the subarray.
-template <typename T>
-__global__ void qs_build_kernel(const QsSeg* list, uint32_t count, T* keys, uint64_t seed,
-                                SegDesc* out) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= count) return;
-  const QsSeg q = list[s];
-  const uint64_t h = sm_stream(seed, q.lo ^ (q.n << 32));
-  const T a = ldk(&keys[q.lo + range_of(sm_stream(h, 0), q.n)]);
-  const T b = ldk(&keys[q.lo + range_of(sm_stream(h, 1), q.n)]);
-  const T c = ldk(&keys[q.lo + range_of(sm_stream(h, 2), q.n)]);
-  const T mx = a > b ? a : b, mn = a > b ? b : a;
-  SegDesc d = {};
-  d.keys = keys + q.lo;
-  d.n = q.n;
-  d.pivot = (uint64_t)(c > mx ? mx : (c < mn ? mn : c));
-  d.salt = q.lo;  // the subarray's place names it, whatever its place in the list
-  out[s] = d;
-}
-
-// Segment records of one slice of the equal-key list: partition by [x < pivot].
-template <typename T>
-__global__ void qs_build_eq_kernel(const QsEq* list, uint32_t count, T* keys, SegDesc* out) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= count) return;
-  const QsEq q = list[s];
-  SegDesc d = {};
-  d.keys = keys + q.lo;
-  d.n = q.n;
-  d.pivot = q.pivot - 1;  // q.pivot > 0 (a zero pivot never reaches this list)
-  d.salt = q.lo;
-  out[s] = d;
-}
-
-__device__ __forceinline__ void qs_push(QsSeg* next, QsSeg* small, QsCounts* c, uint64_t lo,
-                                        uint64_t n) {
-  if (n <= 1) return;  // a single key is in place
-  if (n <= kCut) {
-    small[atomicAdd(&c->small, 1u)] = QsSeg{lo, n};
-    atomicAdd(&c->sort_keys, (unsigned long long)n);
-  } else {
-    next[atomicAdd(&c->next, 1u)] = QsSeg{lo, n};
-  }
-}
-
-// keys the batched launch just before streamed, added to the call's total
-__device__ __forceinline__ void qs_add_traffic(QsCounts* c, const unsigned long long* traffic) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->part_keys += *traffic;
-}
-
-// Children of each partitioned subarray.  A subarray with no successor goes
-// to the equal-key list unless its pivot is 0 (then every key is 0).
-__global__ void qs_split_kernel(const QsSeg* list, uint32_t count, const SegDesc* segs,
-                                const uint64_t* splits, QsSeg* next, QsSeg* small, QsEq* eq,
-                                QsCounts* c, const unsigned long long* traffic) {
-  qs_add_traffic(c, traffic);
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= count) return;
-  const QsSeg q = list[s];
-  const uint64_t t = splits[s];
-  if (t == q.n) {
-    const uint64_t pivot = segs[s].pivot;
-    if (pivot != 0) eq[atomicAdd(&c->eq, 1u)] = QsEq{q.lo, q.n, pivot};
-    return;
-  }
-  qs_push(next, small, c, q.lo, t);
-  qs_push(next, small, c, q.lo + t, q.n - t);
-}
-
-// After the pass by [x < pivot]: [lo, lo + t') stays open, the rest is final.
-__global__ void qs_split_eq_kernel(const QsEq* eq, uint32_t count, const uint64_t* splits,
-                                   QsSeg* next, QsSeg* small, QsCounts* c,
-                                   const unsigned long long* traffic) {
-  qs_add_traffic(c, traffic);
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= count) return;
-  qs_push(next, small, c, eq[s].lo, splits[s]);
-}
-
-// One CTA sorts one subarray of at most kCut keys: bitonic sorting network in
-// shared memory over the next power of two, padded with the largest key.
-constexpr uint32_t kSortThreads = 512;
-
-template <typename T>
-__global__ void __launch_bounds__(kSortThreads) qs_small_sort_kernel(const QsSeg* small,
-                                                                     uint32_t count, T* keys) {
-  __shared__ T buf[kCut];
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t s = blockIdx.x; s < count; s += gridDim.x) {
-    const QsSeg q = small[s];
-    const uint32_t n = (uint32_t)q.n;
-    uint32_t P = 2;
-    while (P < n) P <<= 1;
-    for (uint32_t i = tid; i < P; i += kSortThreads)
-      buf[i] = i < n ? ldk(&keys[q.lo + i]) : (T)~(T)0;
-    __syncthreads();
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        // pair p: i = the p-th index with bit j clear, partner i + j
-        for (uint32_t p = tid; p < (P >> 1); p += kSortThreads) {
-          const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-          const uint32_t l = i + j;
-          const T x = buf[i], y = buf[l];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) { buf[i] = y; buf[l] = x; }
-        }
-        __syncthreads();
-      }
-    }
-    for (uint32_t i = tid; i < n; i += kSortThreads) keys[q.lo + i] = buf[i];
-    __syncthreads();
-  }
-}
-
 struct QsLayout {
-  QsSeg* lists[2];
-  QsEq* eq;
-  QsSeg* small;
+  QsItem* lists[2];
+  QsSmall* small;
   SegDesc* segs;
   uint64_t* splits;
-  QsCounts* counts;
+  QsJob* jobs;                      // one record per slice
+  QsLevelCounts* lc;
+  unsigned long long* acc;          // [0] keys streamed by partitions, [1] keys sorted
   void* batch;
   uint64_t maxseg;
-  uint32_t slice;
+  uint32_t slice, max_slices;
   size_t bytes;
 };
 
 QsLayout qs_layout(void* base, uint64_t n) {
   QsLayout L{};
-  L.maxseg = n / (kCut + 1) + 1;
+  L.maxseg = n / (kQsCut + 1) + 1;
   L.slice = (uint32_t)(L.maxseg < kSlice ? L.maxseg : kSlice);
+  L.max_slices = (uint32_t)((L.maxseg + L.slice - 1) / L.slice);
   unsigned char* p = static_cast<unsigned char*>(base);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -191,30 +51,28 @@ QsLayout qs_layout(void* base, uint64_t n) {
     off += (bytes + 255) / 256 * 256;
     return r;
   };
-  L.lists[0] = reinterpret_cast<QsSeg*>(take(L.maxseg * sizeof(QsSeg)));
-  L.lists[1] = reinterpret_cast<QsSeg*>(take(L.maxseg * sizeof(QsSeg)));
-  L.eq = reinterpret_cast<QsEq*>(take(L.maxseg * sizeof(QsEq)));
-  L.small = reinterpret_cast<QsSeg*>(take(2 * L.maxseg * sizeof(QsSeg)));
+  L.lists[0] = reinterpret_cast<QsItem*>(take(L.maxseg * sizeof(QsItem)));
+  L.lists[1] = reinterpret_cast<QsItem*>(take(L.maxseg * sizeof(QsItem)));
+  L.small = reinterpret_cast<QsSmall*>(take(2 * L.maxseg * sizeof(QsSmall)));
   L.segs = reinterpret_cast<SegDesc*>(take((size_t)L.slice * sizeof(SegDesc)));
   L.splits = reinterpret_cast<uint64_t*>(take((size_t)L.slice * 8));
-  L.counts = reinterpret_cast<QsCounts*>(take(sizeof(QsCounts)));
+  L.jobs = reinterpret_cast<QsJob*>(take((size_t)L.max_slices * sizeof(QsJob)));
+  L.lc = reinterpret_cast<QsLevelCounts*>(take(sizeof(QsLevelCounts)));
+  L.acc = reinterpret_cast<unsigned long long*>(take(16));
   L.batch = take(batch_scratch_bytes(L.slice));
   L.bytes = off;
   return L;
 }
 
-cudaError_t read_counts(const QsLayout& L, QsCounts* host, cudaStream_t st) {
-  cudaError_t e = cudaMemcpyAsync(host, L.counts, sizeof(QsCounts), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e;
-}
-
 }  // namespace
 
 size_t quicksort_scratch_bytes(uint64_t n) { return qs_layout(nullptr, n).bytes; }
+size_t quicksort_staging_bytes(uint64_t n) {
+  return (size_t)qs_layout(nullptr, n).max_slices * sizeof(QsJob) + 64;
+}
 
 template <typename T>
-cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* host_words,
+cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* staging,
                              const BatchTuning& tune, uint32_t* bar, uint32_t* status,
                              LaunchCfg& cfg, const cudaEvent_t* ev, SortStats* stats) {
   cudaStream_t st = cfg.stream;
@@ -222,91 +80,93 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
   if (n < 2) return cudaSuccess;
   const QsLayout L = qs_layout(scratch, n);
   const BatchScratch Bs = carve_batch_scratch(L.batch, L.slice, bar, status);
-  QsCounts* hc = static_cast<QsCounts*>(host_words);
-  cudaError_t e;
-  uint64_t open = 0;
-  uint32_t nsmall = 0, cur = 0, levels = 0;
-  e = cudaMemsetAsync(L.counts, 0, sizeof(QsCounts), st);
+  QsJob* hjobs = static_cast<QsJob*>(staging);
+  unsigned char* hback = static_cast<unsigned char*>(staging) + L.max_slices * sizeof(QsJob);
+  const uint64_t batch_seed = sm_stream(seed, 0x51);
+  cudaError_t e = cudaMemsetAsync(L.acc, 0, 16, st);
   if (e != cudaSuccess) return e;
-  {
-    const QsSeg whole{0, n};
-    // the whole array is the first open subarray, or the only small one
-    e = cudaMemcpyAsync(n > kCut ? L.lists[0] : L.small, &whole, sizeof(QsSeg),
-                        cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    if (n > kCut) open = 1; else nsmall = 1;
+  // the first level: the whole array as one item, or as the only small subarray
+  uint64_t open = 0;
+  if (n > kQsCut) {
+    const QsItem whole{0, n, 0, 0};
+    e = cudaMemcpyAsync(L.lists[0], &whole, sizeof(whole), cudaMemcpyHostToDevice, st);
+    open = 1;
+  } else {
+    const QsSmall whole{0, n};
+    e = cudaMemcpyAsync(L.small, &whole, sizeof(whole), cudaMemcpyHostToDevice, st);
   }
-  // optional timing: events around a stretch of launches, read after the
-  // host's next synchronisation of the stream
+  if (e != cudaSuccess) return e;
+  const QsLevelCounts first{0, n > kQsCut ? 0u : 1u};
+  e = cudaMemcpyAsync(L.lc, &first, sizeof(first), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
   auto mark = [&](int k) -> cudaError_t { return ev ? cudaEventRecord(ev[k], st) : cudaSuccess; };
-  auto elapsed = [&](float* acc) {
+  auto elapsed = [&](int a, int b, float* acc) {
     float ms = 0.f;
-    if (ev && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) *acc += ms;
+    if (ev && cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess) *acc += ms;
   };
-  auto sort_small = [&](uint32_t cnt) -> cudaError_t {
-    if (cnt == 0) return cudaSuccess;
-    const uint32_t grid = cnt < 8192 ? cnt : 8192;
-    cudaError_t r = mark(0);
-    if (r != cudaSuccess) return r;
-    qs_small_sort_kernel<T><<<grid, kSortThreads, 0, st>>>(L.small, cnt, keys);
-    cfg.launches++;
-    if ((r = cudaGetLastError()) != cudaSuccess) return r;
-    if (ev) {
-      if ((r = mark(1)) != cudaSuccess || (r = cudaEventSynchronize(ev[1])) != cudaSuccess)
-        return r;
-      elapsed(&stats->sort_ms);
+  uint32_t cur = 0, levels = 0;
+  for (;;) {
+    // one record per slice of the level's list (one record, of no items,
+    // for the small-only first level: the small sort reads its lists)
+    const uint32_t nslices = (uint32_t)((open + L.slice - 1) / L.slice);
+    const uint32_t nrec = nslices ? nslices : 1;
+    for (uint32_t k = 0; k < nrec; k++) {
+      const uint64_t o = (uint64_t)k * L.slice;
+      QsJob& J = hjobs[k];
+      J.keys = keys;
+      J.items = L.lists[cur] + o;
+      J.next = L.lists[cur ^ 1];
+      J.small = L.small;
+      J.lc = L.lc;
+      J.sort_keys = L.acc + 1;
+      J.seed = seed;
+      J.level = levels;
+      J.count = (uint32_t)(open > o ? (open - o < L.slice ? open - o : L.slice) : 0);
+      J.seg_base = 0;
+      J.pad = 0;
     }
-    return cudaSuccess;
-  };
-  const unsigned long long* traffic = Bs.totals + 2;
-  while (open > 0) {
-    if (++levels > kMaxSortLevels) return cudaErrorUnknown;  // sizes shrink every level
-    QsSeg* list = L.lists[cur];
-    QsSeg* next = L.lists[cur ^ 1];
-    e = cudaMemsetAsync(L.counts, 0, 16, st);  // the level's list sizes
+    if (levels > 0) e = cudaMemsetAsync(L.lc, 0, sizeof(QsLevelCounts), st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(L.jobs, hjobs, nrec * sizeof(QsJob), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = mark(0);
     if (e != cudaSuccess) return e;
-    for (uint64_t o = 0; o < open; o += L.slice) {
-      const uint32_t cnt = (uint32_t)(open - o < L.slice ? open - o : L.slice);
-      const unsigned blocks = (cnt + 255) / 256;
-      qs_build_kernel<T><<<blocks, 256, 0, st>>>(list + o, cnt, keys, seed + levels, L.segs);
+    for (uint32_t k = 0; k < nslices; k++) {
+      const uint32_t cnt = hjobs[k].count;
+      const dim3 grid((cnt + 255) / 256, 1);
+      qs_build_kernel<T><<<grid, 256, 0, st>>>(L.jobs + k, L.segs);
       cfg.launches++;
-      e = launch_batched<T>(L.segs, cnt, sm_stream(seed, levels), L.splits, Bs, tune, cfg);
+      e = launch_batched<T>(L.segs, cnt, batch_seed, L.splits, Bs, tune, cfg);
       if (e != cudaSuccess) return e;
-      qs_split_kernel<<<blocks, 256, 0, st>>>(list + o, cnt, L.segs, L.splits, next, L.small,
-                                              L.eq, L.counts, traffic);
+      qs_split_kernel<<<grid, 256, 0, st>>>(L.jobs + k, L.segs, L.splits, Bs.totals + 2, L.acc);
       cfg.launches++;
     }
     if ((e = mark(1)) != cudaSuccess) return e;
-    if ((e = read_counts(L, hc, st)) != cudaSuccess) return e;
-    elapsed(&stats->partition_ms);
-    const uint32_t neq = hc->eq;
-    if (neq > 0 && (e = mark(0)) != cudaSuccess) return e;
-    for (uint32_t o = 0; o < neq; o += L.slice) {  // split off the keys equal to the pivot
-      const uint32_t cnt = neq - o < L.slice ? neq - o : L.slice;
-      const unsigned blocks = (cnt + 255) / 256;
-      qs_build_eq_kernel<T><<<blocks, 256, 0, st>>>(L.eq + o, cnt, keys, L.segs);
-      cfg.launches++;
-      e = launch_batched<T>(L.segs, cnt, sm_stream(~seed, levels), L.splits, Bs, tune, cfg);
-      if (e != cudaSuccess) return e;
-      qs_split_eq_kernel<<<blocks, 256, 0, st>>>(L.eq + o, cnt, L.splits, next, L.small,
-                                                 L.counts, traffic);
-      cfg.launches++;
-    }
-    if (neq > 0) {
-      if ((e = mark(1)) != cudaSuccess) return e;
-      if ((e = read_counts(L, hc, st)) != cudaSuccess) return e;
-      elapsed(&stats->partition_ms);
-    }
-    if ((e = sort_small(hc->small)) != cudaSuccess) return e;
-    open = hc->next;
+    // the level's small subarrays (at most two per item; the count is read on the device)
+    const uint64_t small_bound = open ? 2 * open : 1;
+    const dim3 sgrid((unsigned)(small_bound < 8192 ? small_bound : 8192), 1);
+    qs_small_sort_kernel<T><<<sgrid, kQsSortThreads, 0, st>>>(L.jobs);
+    cfg.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(hback, L.lc, sizeof(QsLevelCounts), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    elapsed(0, 1, &stats->partition_ms);
+    elapsed(1, 2, &stats->sort_ms);
+    if (nslices == 0) break;  // the small-only first level is done
+    levels++;
+    open = reinterpret_cast<const QsLevelCounts*>(hback)->next;
     cur ^= 1;
+    if (open == 0) break;
+    if (levels > kMaxSortLevels) return cudaErrorUnknown;  // sizes shrink every level
   }
-  if ((e = sort_small(nsmall)) != cudaSuccess) return e;
-  if ((e = read_counts(L, hc, st)) != cudaSuccess) return e;
+  e = cudaMemcpyAsync(hback, L.acc, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  const unsigned long long* acc = reinterpret_cast<const unsigned long long*>(hback);
   stats->levels = levels;
-  stats->partition_keys = hc->part_keys;
-  stats->sort_keys = hc->sort_keys + (n <= kCut ? n : 0);
+  stats->partition_keys = acc[0];
+  stats->sort_keys = acc[1] + (n <= kQsCut ? n : 0);
   return cudaGetLastError();
 }
 
