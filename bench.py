@@ -61,13 +61,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--seed", type=int, default=0xC0FF2)
-    ap.add_argument("--workload", choices=["partition", "quicksort", "batched"],
+    ap.add_argument("--workload", choices=["partition", "quicksort", "batched", "serve"],
                     default="partition",
                     help="partition (default): one 2^30-key partition; quicksort: 2^28 uint64 "
-                         "sort; batched: 4096 partitions of log-uniform sizes in one graph")
+                         "sort; batched: 4096 partitions of log-uniform sizes in one graph; "
+                         "serve: Poisson stream of partition and sort requests")
     ap.add_argument("--input", choices=["uniform", "sorted", "reverse", "dup16"],
                     default="uniform", help="quicksort input")
     ap.add_argument("--instances", type=int, default=4096, help="batched: instance count")
+    ap.add_argument("--requests", type=int, default=1000, help="serve: requests per step")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per s")
+    ap.add_argument("--budget-gib", type=float, default=64.0, help="serve: HBM budget")
+    ap.add_argument("--slots", type=int, default=256, help="serve: requests in flight, at most")
     return ap.parse_args()
 
 
@@ -189,6 +194,8 @@ def run_reference(args):
         return run_reference_sort(args)
     if args.workload == "batched":
         return run_reference_batched(args)
+    if args.workload == "serve":
+        return run_reference_serve(args)
     import oracle
     pivot = inputs.quantile_pivot(1, 2)
     log2s = min(args.log2n, 26)
@@ -218,11 +225,11 @@ def run_reference(args):
     }))
 
 
-def reference_line(args, metric, value, unit, ms, workload, oracle_kind, sample):
+def reference_line(args, metric, value, unit, ms, workload, oracle_kind, sample, dtype="u64"):
     print(json.dumps({
         "impl": "reference", "metric": metric, "value": value, "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic", "config": {"workload": workload, "oracle": oracle_kind},
         "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -267,6 +274,40 @@ def run_reference_batched(args):
                    "batched partition, %d instances" % args.instances,
                    "serial two-pointer partition per instance (CPU)",
                    "about 2 s of instances per step, in batch order")
+
+
+def run_reference_serve(args):
+    """The oracle serving the same request mix one request at a time on one host
+    core (partition: two-pointer; sort: serial quicksort), on a bounded sample."""
+    import oracle
+    rng = np.random.default_rng(args.seed)
+    sizes = inputs.log_uniform_sizes(4096, args.seed, 10, 26)
+    vals, keys_all = [], 0
+    for k in range(args.warmup + args.steps):
+        spent, keys = 0.0, 0
+        for i, m in enumerate(sizes):
+            if spent > 1.0:
+                break
+            bits = 64 if rng.random() < 0.5 else 32
+            a = inputs.uniform_u64(int(m), args.seed + i) if bits == 64 else \
+                inputs.uniform_u32(int(m), args.seed + i)
+            t0 = time.perf_counter()
+            if rng.random() < 0.3:
+                oracle.quicksort(a, i)
+            else:
+                oracle.partition(a, inputs.quantile_pivot(int(rng.integers(1, 100)), 100, bits))
+            spent += time.perf_counter() - t0
+            keys += int(m)
+        if k >= args.warmup:
+            vals.append(keys / spent / 1e9)
+            keys_all += keys
+    v = statistics.mean(vals)
+    reference_line(args, "served keys/s (Poisson %.0f req/s, 70%% partition / 30%% sort, sizes "
+                   "log-uniform [2^10, 2^26], uint32/uint64)" % args.rate, v, "Gkeys/s",
+                   keys_all / args.steps / (v * 1e9) * 1e3,
+                   "serve, requests one at a time", "serial partition / quicksort per request",
+                   "requests in stream order until 1 s of service time is spent (one large "
+                   "sort can overrun it), service time only", dtype="u32+u64")
 
 
 def run_ours(args):
@@ -788,6 +829,125 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serve
+
+def serve_requests(lp, count, rate, seed):
+    """Poisson arrivals (mean `rate` per s), 70% partition / 30% sort, sizes
+    log-uniform in [2^10, 2^26], uint32 or uint64 keys with equal probability,
+    uniform keys generated on the device from each request's seed; a
+    partition's pivot is the key value at a seeded quantile in [1%, 99%]."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    t -= t[0]
+    sizes = inputs.log_uniform_sizes(count, seed, 10, 26)
+    reqs = []
+    for i in range(count):
+        kind = lp.LP_REQ_SORT if rng.random() < 0.3 else lp.LP_REQ_PARTITION
+        bits = 64 if rng.random() < 0.5 else 32
+        pivot = inputs.quantile_pivot(int(rng.integers(1, 100)), 100, bits)
+        reqs.append(lp.Server.request(kind, bits, int(sizes[i]), pivot,
+                                      (seed << 20) + i, None, float(t[i])))
+    return reqs
+
+
+def latency_summary(reqs, out):
+    lat = np.array([c["done_s"] - c["arrival_s"] for c in out]) * 1e3
+    keys = sum(r.n for r in reqs)
+    span = max(c["done_s"] for c in out) - min(c["arrival_s"] for c in out)
+    part = [l for r, l in zip(reqs, lat) if r.kind == 0]
+    sort = [l for r, l in zip(reqs, lat) if r.kind == 1]
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "p50_partition_ms": float(np.percentile(part, 50)) if part else None,
+            "p99_partition_ms": float(np.percentile(part, 99)) if part else None,
+            "p50_sort_ms": float(np.percentile(sort, 50)) if sort else None,
+            "p99_sort_ms": float(np.percentile(sort, 99)) if sort else None,
+            "keys": keys, "span_s": span, "gkeys_per_s": keys / span / 1e9}
+
+
+def run_serve(args):
+    import torch
+    ws, rank, local = dist_env()
+    init_dist(local, ws)
+    from paper_2004_12532_gb300 import binding as lp
+    budget = int(args.budget_gib * (1 << 30))
+    srv = lp.Server(local, budget_bytes=budget, max_slots=args.slots, seed=args.seed,
+                    timing=True)
+    seed0 = args.seed + 7919 * rank
+    for w in range(args.warmup):
+        srv.run(serve_requests(lp, max(50, args.requests // 10), args.rate, seed0 + 900 + w))
+    st0 = srv.stats()
+    s64_0, s32_0 = srv.streamed_keys()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    summaries, all_lat, keys_total, span_total = [], [], 0, 0.0
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        reqs = serve_requests(lp, args.requests, args.rate, seed0 + k)
+        out = srv.run(reqs)
+        summ = latency_summary(reqs, out)
+        summaries.append(summ)
+        all_lat += [(c["done_s"] - c["arrival_s"]) * 1e3 for c in out]
+        keys_total += summ["keys"]
+        span_total += summ["span_s"]
+    wall_s = time.perf_counter() - wall0
+    clk = clocks.stop()
+    st1 = srv.stats()
+    s64_1, s32_1 = srv.streamed_keys()
+    # the first step's requests again, one at a time through the plain calls
+    reqs0 = serve_requests(lp, args.requests, args.rate, seed0)
+    base = latency_summary(reqs0, srv.run(reqs0, mode=lp.LP_SERVE_ONE_AT_A_TIME))
+    ms = span_total / args.steps * 1e3
+    ms_all = max_over_ranks(ws, ms)
+    value = ws * keys_total / args.steps / (ms_all / 1e3) / 1e9
+    lat = np.array(all_lat)
+    peak, peak_kind = measured_peaks()
+    b_ms = st1["batched_ms"] - st0["batched_ms"]
+    b_bytes = 2 * (8 * (s64_1 - s64_0) + 4 * (s32_1 - s32_0))
+    achieved = b_bytes / (b_ms / 1e3) / 1e9 if b_ms > 0 else None
+    result = {
+        "metric": "served keys/s (Poisson %.0f req/s, 70%% partition / 30%% sort, sizes "
+                  "log-uniform [2^10, 2^26], uint32/uint64)" % args.rate,
+        "value": value, "unit": "Gkeys/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64",
+        "data": "synthetic (seeded Poisson arrivals; uniform keys generated on the device "
+                "from each request's seed on admission)",
+        "config": {"workload": "serve %d requests per step at %.0f req/s" % (
+                       args.requests, args.rate),
+                   "budget_gib": args.budget_gib, "slots": args.slots,
+                   "requests_per_step": args.requests,
+                   "l2": "request keys regenerated on admission; working set above L2",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "latency": {"p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)),
+                    "per_step": summaries},
+        "one_at_a_time": base,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "batched_kernel (uint64 and uint32 launches of the engine "
+                               "steps)", "peak_kind": peak_kind,
+                     "algorithmic_bytes": b_bytes, "ms": b_ms},
+        "engine": {"steps": st1["steps"] - st0["steps"],
+                   "launches": st1["launches"] - st0["launches"],
+                   "peak_bytes": st1["peak_bytes"], "engine_bytes": st1["engine_bytes"],
+                   "busy_s": st1["busy_s"] - st0["busy_s"]},
+        "gpu_launches": st1["launches"] - st0["launches"],
+        "e2e": None,
+        "e2e_note": "requests' keys are device-resident by design (generated on admission)",
+        "wall_s_timed_region": wall_s,
+    }
+    if clk:
+        result["clocks"] = clk
+    srv.close()
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.log2n is None:
@@ -799,6 +959,8 @@ def main():
         run_quicksort(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -249,7 +249,7 @@ typedef struct {
   uint32_t max_segments;  /* segment records per key width per step (0: 65536) */
   uint64_t seed;          /* seeds the offsets X of every batched launch */
   uint32_t keep_results;  /* 1: finished requests keep their keys until lp_server_release */
-  uint32_t pad;
+  uint32_t timing;        /* 1: CUDA events time every batched launch (stats.batched_ms) */
 } lp_server_config;
 
 enum { LP_REQ_PARTITION = 0, LP_REQ_SORT = 1 };
@@ -281,6 +281,7 @@ typedef struct {
   uint64_t peak_bytes;    /* arena bytes in use, at most */
   uint64_t budget_bytes, in_use_bytes, engine_bytes;
   double busy_s;          /* host time spent in engine steps */
+  double batched_ms;      /* device time of the batched launches (config.timing) */
 } lp_server_stats;
 
 /* Errors: LP_ERR_INVALID_ARG (bad config), LP_ERR_OOM (the budget or the
@@ -306,8 +307,9 @@ lp_status lp_server_result(lp_server *server, uint64_t id, void **d_keys_out);
 lp_status lp_server_fetch(lp_server *server, uint64_t id, void *dst, uint64_t bytes);
 lp_status lp_server_release(lp_server *server, uint64_t id);
 lp_status lp_server_get_stats(const lp_server *server, lp_server_stats *out);
-/* Keys streamed by all batched launches of the engine (read once, written once). */
-lp_status lp_server_streamed_keys(lp_server *server, uint64_t *keys_out);
+/* Keys streamed (read once, written once) by all batched launches of the
+ * engine, per key width. */
+lp_status lp_server_streamed_keys(lp_server *server, uint64_t *keys_u64, uint64_t *keys_u32);
 /* Open-loop driver: submits reqs[i] at arrival_s seconds after the call
  * begins (arrivals in time order), steps the engine until every request is
  * done and writes request i's record to out[i].  LP_SERVE_ONE_AT_A_TIME runs

@@ -51,7 +51,7 @@ class lp_sort_stats(C.Structure):
 class lp_server_config(C.Structure):
     _fields_ = [("budget_bytes", C.c_uint64), ("max_slots", C.c_uint32),
                 ("max_segments", C.c_uint32), ("seed", C.c_uint64),
-                ("keep_results", C.c_uint32), ("pad", C.c_uint32)]
+                ("keep_results", C.c_uint32), ("timing", C.c_uint32)]
 
 
 class lp_request(C.Structure):
@@ -71,7 +71,8 @@ class lp_server_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("launches", C.c_uint64), ("completed", C.c_uint64),
                 ("keys_done", C.c_uint64), ("peak_bytes", C.c_uint64),
                 ("budget_bytes", C.c_uint64), ("in_use_bytes", C.c_uint64),
-                ("engine_bytes", C.c_uint64), ("busy_s", C.c_double)]
+                ("engine_bytes", C.c_uint64), ("busy_s", C.c_double),
+                ("batched_ms", C.c_double)]
 
 
 _SIGS = {
@@ -119,7 +120,7 @@ _SIGS = {
     "lp_server_fetch": (_i, [_p, _u64, _p, _u64]),
     "lp_server_release": (_i, [_p, _u64]),
     "lp_server_get_stats": (_i, [_p, _p]),
-    "lp_server_streamed_keys": (_i, [_p, _pu64]),
+    "lp_server_streamed_keys": (_i, [_p, _pu64, _pu64]),
     "lp_server_run": (_i, [_p, _p, _u32, _u32, _p]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
@@ -442,11 +443,11 @@ class Server:
     """lp_server: continuous-batching engine for partition and sort requests."""
 
     def __init__(self, device=None, budget_bytes=1 << 30, max_slots=0, max_segments=0, seed=1,
-                 keep_results=False):
+                 keep_results=False, timing=False):
         if device is None:
             device = torch.cuda.current_device()
         cfg = lp_server_config(int(budget_bytes), int(max_slots), int(max_segments), int(seed),
-                               1 if keep_results else 0, 0)
+                               1 if keep_results else 0, 1 if timing else 0)
         h = C.c_void_p()
         st = lib().lp_server_create(int(device), C.byref(cfg), C.byref(h))
         if st != LP_OK:
@@ -514,9 +515,10 @@ class Server:
         return {f: getattr(st, f) for f, _ in lp_server_stats._fields_}
 
     def streamed_keys(self):
-        k = C.c_uint64()
-        self.check(lib().lp_server_streamed_keys(self.h, C.byref(k)))
-        return int(k.value)
+        """(uint64 keys, uint32 keys) streamed by the engine's batched launches."""
+        a, b = C.c_uint64(), C.c_uint64()
+        self.check(lib().lp_server_streamed_keys(self.h, C.byref(a), C.byref(b)))
+        return int(a.value), int(b.value)
 
     def run(self, requests, mode=LP_SERVE_CONTINUOUS):
         """Open-loop run of lp_request records (arrival_s relative to the start)."""

@@ -126,7 +126,9 @@ struct lp_server {
   WidthBufs w[2];                      // [0] uint64 keys, [1] uint32 keys
   QsLevelCounts* d_lc = nullptr;       // per slot
   unsigned long long* d_sorted = nullptr;  // per slot: keys sorted in shared memory
-  unsigned long long* d_acc = nullptr;     // keys streamed by all batched launches
+  unsigned long long* d_acc = nullptr;     // keys streamed by batched launches, per width
+  cudaEvent_t ev[4] = {};                  // around each width's batched launch
+  bool timed[2] = {false, false};
   QsBegin* d_begin = nullptr;
   uint32_t* d_ctl = nullptr;           // grid barrier (2 words), status
   // pinned staging
@@ -253,16 +255,21 @@ cudaError_t run_width(lp_server* s, int k, uint32_t nparts, uint32_t njobs, uint
     cfg.launches++;
   }
   if (nsegs > 0) {
+    if (s->ev[0] && (e = cudaEventRecord(s->ev[2 * k], st)) != cudaSuccess) return e;
     e = lp::launch_batched<T>(W.segs, nsegs, s->cfg.seed, W.splits, W.B, tune, cfg);
     if (e != cudaSuccess) return e;
+    if (s->ev[0]) {
+      if ((e = cudaEventRecord(s->ev[2 * k + 1], st)) != cudaSuccess) return e;
+      s->timed[k] = true;
+    }
     // children of the sorts' items; the keys this launch streamed go to the
     // engine's total
     if (njobs > 0 && max_open > 0) {
       const dim3 grid((unsigned)((max_open + 255) / 256), njobs);
       lp::qs_split_kernel<<<grid, 256, 0, st>>>(W.jobs, W.segs, W.splits, W.B.totals + 2,
-                                                s->d_acc);
+                                                s->d_acc + k);
     } else {
-      add_traffic_kernel<<<1, 1, 0, st>>>(W.B.totals + 2, s->d_acc);
+      add_traffic_kernel<<<1, 1, 0, st>>>(W.B.totals + 2, s->d_acc + k);
     }
     cfg.launches++;
   }
@@ -416,6 +423,7 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
       e = cudaGetLastError();
     }
   }
+  s->timed[0] = s->timed[1] = false;
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ctl + 2, 0, 8, st);  // both status words
   if (e == cudaSuccess)
     e = run_width<uint64_t>(s, 0, nparts[0], njobs[0], nsegs[0], max_open[0], max_small[0]);
@@ -440,6 +448,11 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
                     "device status after an engine step");
   }
   s->stats.steps++;
+  for (int k = 0; k < 2; k++) {
+    float ms = 0.f;
+    if (s->timed[k] && cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]) == cudaSuccess)
+      s->stats.batched_ms += ms;
+  }
   // ---- outcomes
   std::vector<uint64_t> finished;
   for (int k = 0; k < 2; k++) {
@@ -600,6 +613,9 @@ lp_status lp_server_create(int device, const lp_server_config* cfg, lp_server** 
   s->stage_bytes = stage_layout(nullptr, slots).bytes;
   if (cudaMallocHost(&s->h_stage, s->stage_bytes) != cudaSuccess) return fail(LP_ERR_OOM);
   for (uint32_t i = 0; i < slots; i++) s->free_slots.push_back(slots - 1 - i);
+  if (s->cfg.timing)
+    for (int i = 0; i < 4; i++)
+      if (cudaEventCreate(&s->ev[i]) != cudaSuccess) return fail(LP_ERR_CUDA);
   s->stats.engine_bytes = engine_bytes(C, slots);
   *out = s;
   return LP_OK;
@@ -608,6 +624,8 @@ lp_status lp_server_create(int device, const lp_server_config* cfg, lp_server** 
 lp_status lp_server_destroy(lp_server* s) {
   if (!s) return LP_ERR_INVALID_ARG;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  for (int i = 0; i < 4; i++)
+    if (s->ev[i]) cudaEventDestroy(s->ev[i]);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->d_engine) cudaFree(s->d_engine);
   if (s->d_arena) cudaFree(s->d_arena);
@@ -695,14 +713,15 @@ lp_status lp_server_get_stats(const lp_server* s, lp_server_stats* out) {
   return LP_OK;
 }
 
-lp_status lp_server_streamed_keys(lp_server* s, uint64_t* keys_out) {
-  if (!s || !keys_out) return LP_ERR_INVALID_ARG;
-  unsigned long long v = 0;
-  cudaError_t e = cudaMemcpyAsync(s->h_stage, s->d_acc, 8, cudaMemcpyDeviceToHost, s->stream);
+lp_status lp_server_streamed_keys(lp_server* s, uint64_t* keys_u64, uint64_t* keys_u32) {
+  if (!s || !keys_u64 || !keys_u32) return LP_ERR_INVALID_ARG;
+  unsigned long long v[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(s->h_stage, s->d_acc, 16, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return srv_cuda(s, e, "read streamed keys");
-  memcpy(&v, s->h_stage, 8);
-  *keys_out = v;
+  memcpy(v, s->h_stage, 16);
+  *keys_u64 = v[0];
+  *keys_u32 = v[1];
   return LP_OK;
 }
 
