@@ -389,13 +389,8 @@ def run_ours(args):
     t = int(d_split.item())
 
     ms = sum(part_ms) / len(part_ms)
-    ms_all = ms
-    if ws > 1:
-        import torch.distributed as dist
-        x = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms_all = float(x.item())
-    value = ws * 3 * E * n / (ms_all / 1e3) / 1e9
+    bytes_all, ms_all = whole_job(ws, 3 * E * n, ms)
+    value = bytes_all / (ms_all / 1e3) / 1e9
 
     peak, peak_kind = measured_peaks()
     k_ms = sum(kern_ms) / len(kern_ms)
@@ -535,14 +530,20 @@ def init_dist(local, ws):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
 
-def max_over_ranks(ws, ms):
+def whole_job(ws, units, ms):
+    """(sum of units over ranks, max of ms over ranks): the whole-job work and
+    its time.  Single process: (units, ms).  The reduction runs on the
+    process group's device (CUDA under NCCL, the host under gloo)."""
     if ws == 1:
-        return ms
+        return float(units), float(ms)
     import torch
     import torch.distributed as dist
-    x = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    dist.all_reduce(x, op=dist.ReduceOp.MAX)
-    return float(x.item())
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
 
 
 def run_quicksort(args):
@@ -586,8 +587,8 @@ def run_quicksort(args):
     key = unsigned_order(keys)
     sorted_ok = bool((key[1:] >= key[:-1]).all())
     ms = sum(step_ms) / len(step_ms)
-    ms_all = max_over_ranks(ws, ms)
-    value = ws * n / (ms_all / 1e3) / 1e9
+    keys_all, ms_all = whole_job(ws, n, ms)
+    value = keys_all / (ms_all / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     pk = sum(s["partition_keys"] for s in stats) / len(stats)
     pms = sum(s["partition_ms"] for s in stats) / len(stats)
@@ -752,8 +753,8 @@ def run_batched(args):
         p_ms.append(ev0.elapsed_time(ev1))
     same_splits = bool(torch.equal(splits, splits_plain))
     ms = sum(g_ms) / len(g_ms)
-    ms_all = max_over_ranks(ws, ms)
-    value = ws * keys_total / (ms_all / 1e3) / 1e9
+    keys_all, ms_all = whole_job(ws, keys_total, ms)
+    value = keys_all / (ms_all / 1e3) / 1e9
     plain_ms = sum(p_ms) / len(p_ms)
     peak, peak_kind = measured_peaks()
     sk = sum(streamed) / len(streamed)
@@ -900,8 +901,8 @@ def run_serve(args):
     reqs0 = serve_requests(lp, args.requests, args.rate, seed0)
     base = latency_summary(reqs0, srv.run(reqs0, mode=lp.LP_SERVE_ONE_AT_A_TIME))
     ms = span_total / args.steps * 1e3
-    ms_all = max_over_ranks(ws, ms)
-    value = ws * keys_total / args.steps / (ms_all / 1e3) / 1e9
+    keys_all, ms_all = whole_job(ws, keys_total / args.steps, ms)
+    value = keys_all / (ms_all / 1e3) / 1e9
     lat = np.array(all_lat)
     peak, peak_kind = measured_peaks()
     b_ms = st1["batched_ms"] - st0["batched_ms"]
