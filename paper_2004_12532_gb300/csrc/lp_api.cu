@@ -10,6 +10,7 @@
 #include "../../include/libpartition.h"
 #include "lp_batched.h"
 #include "lp_ctx.h"
+#include "lp_qs.cuh"
 #include "lp_device.cuh"
 #include "lp_launch.h"
 #include "lp_plan.h"
@@ -265,7 +266,8 @@ lp_status lp_ctx_create(lp_ctx** out, int device) {
       (e = lp::streaming_grid<uint32_t, false>(device, &c->grid_u32)) != cudaSuccess ||
       (e = lp::streaming_grid<uint64_t, true>(device, &c->grid_kv)) != cudaSuccess ||
       (e = lp::batched_prepare<uint64_t>(device, &c->grid_batch_u64)) != cudaSuccess ||
-      (e = lp::batched_prepare<uint32_t>(device, &c->grid_batch_u32)) != cudaSuccess) {
+      (e = lp::batched_prepare<uint32_t>(device, &c->grid_batch_u32)) != cudaSuccess ||
+      (e = lp::qs_prepare()) != cudaSuccess) {
     delete c;
     return LP_ERR_CUDA;
   }

@@ -1,7 +1,7 @@
-// lp_qs.cuh -- device side of the quicksort on the partition (Sec. 5, "A
-// Full Quicksort"), shared by the one-array quicksort (lp_quicksort.cu) and
-// the serving engine (lp_server.cu), which runs the levels of many sorts in
-// the same batched launches.
+// lp_qs.cuh -- the quicksort on the partition (Sec. 5, "A Full Quicksort"):
+// records and kernel launchers (kernels in lp_qs.cu) shared by the one-array
+// quicksort (lp_quicksort.cu) and the serving engine (lp_server.cu), which
+// runs the levels of many sorts in the same batched launches.
 //
 // A sort job owns an item list per level.  An item is an open subarray
 // [lo, lo + n) with n > kQsCut:
@@ -54,105 +54,25 @@ struct QsJob {
   uint32_t pad;
 };
 
+// Segment records of every job in `jobs` (grid.y = jobs, x covers the
+// largest item count): median-of-3 pivots, equal-key pivots minus one.
 template <typename T>
-__device__ __forceinline__ T qs_ld(const T* p) {
-  if constexpr (sizeof(T) == 8) return (T)__ldcg(reinterpret_cast<const unsigned long long*>(p));
-  else return (T)__ldcg(reinterpret_cast<const unsigned int*>(p));
-}
+cudaError_t launch_qs_build(const QsJob* jobs, uint32_t njobs, uint32_t max_count, SegDesc* segs,
+                            cudaStream_t st);
 
-// Segment records of every job slice: blockIdx.y = job, x = item.
+// Children of every partitioned item after the batched launch; adds the keys
+// that launch streamed (*traffic) to *traffic_acc.
+cudaError_t launch_qs_split(const QsJob* jobs, uint32_t njobs, uint32_t max_count,
+                            const SegDesc* segs, const uint64_t* splits,
+                            const unsigned long long* traffic, unsigned long long* traffic_acc,
+                            cudaStream_t st);
+
+// Sorts every job's small list in shared memory; `ctas` CTAs per job.
 template <typename T>
-__global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
-  const QsJob& J = jobs[blockIdx.y];
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= J.count) return;
-  const QsItem q = J.items[i];
-  T* keys = static_cast<T*>(J.keys);
-  const uint64_t h = sm_stream(J.seed + J.level, q.lo ^ (q.n << 32));
-  SegDesc d = {};
-  d.keys = keys + q.lo;
-  d.n = q.n;
-  if (q.eq) {
-    d.pivot = q.pivot - 1;  // q.pivot > 0: a zero pivot never makes an equal-key item
-  } else {
-    const T a = qs_ld(&keys[q.lo + range_of(sm_stream(h, 0), q.n)]);
-    const T b = qs_ld(&keys[q.lo + range_of(sm_stream(h, 1), q.n)]);
-    const T c = qs_ld(&keys[q.lo + range_of(sm_stream(h, 2), q.n)]);
-    const T mx = a > b ? a : b, mn = a > b ? b : a;
-    d.pivot = (uint64_t)(c > mx ? mx : (c < mn ? mn : c));
-  }
-  d.salt = sm_stream(h, 3);  // the subarray and level name it, not its place in the list
-  segs[J.seg_base + i] = d;
-}
+cudaError_t launch_qs_small_sort(const QsJob* jobs, uint32_t njobs, uint32_t ctas,
+                                 cudaStream_t st);
 
-static __device__ __forceinline__ void qs_push(const QsJob& J, uint64_t lo, uint64_t n) {
-  if (n <= 1) return;  // a single key is in place
-  if (n <= kQsCut) {
-    J.small[atomicAdd(&J.lc->small, 1u)] = QsSmall{lo, n};
-    atomicAdd(J.sort_keys, (unsigned long long)n);
-  } else {
-    J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{lo, n, 0, 0};
-  }
-}
-
-// Children of every partitioned item (after the batched launch); the keys the
-// launch streamed are added to *traffic_acc.
-static __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const uint64_t* splits,
-                                const unsigned long long* traffic,
-                                unsigned long long* traffic_acc) {
-  const QsJob& J = jobs[blockIdx.y];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *traffic_acc += *traffic;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= J.count) return;
-  const QsItem q = J.items[i];
-  const uint64_t t = splits[J.seg_base + i];
-  if (q.eq) {  // [lo, lo + t) < p; the rest equals p
-    qs_push(J, q.lo, t);
-    return;
-  }
-  if (t == q.n) {  // no successor: split off the keys equal to the pivot next level
-    const uint64_t p = segs[J.seg_base + i].pivot;
-    if (p != 0) J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{q.lo, q.n, p, 1};
-    return;
-  }
-  qs_push(J, q.lo, t);
-  qs_push(J, q.lo + t, q.n - t);
-}
-
-// Every job's small list, one subarray per CTA at a time: bitonic sorting
-// network in shared memory over the next power of two, padded with the
-// largest key; blockIdx.y = job.  The list size is read on the device.
-template <typename T>
-__global__ void __launch_bounds__(kQsSortThreads) qs_small_sort_kernel(const QsJob* jobs) {
-  __shared__ T buf[kQsCut];
-  const QsJob& J = jobs[blockIdx.y];
-  const uint32_t tid = threadIdx.x;
-  const uint32_t cnt = *reinterpret_cast<volatile uint32_t*>(&J.lc->small);
-  T* keys = static_cast<T*>(J.keys);
-  for (uint32_t s = blockIdx.x; s < cnt; s += gridDim.x) {
-    const QsSmall q = J.small[s];
-    const uint32_t n = (uint32_t)q.n;
-    uint32_t P = 2;
-    while (P < n) P <<= 1;
-    for (uint32_t i = tid; i < P; i += kQsSortThreads)
-      buf[i] = i < n ? qs_ld(&keys[q.lo + i]) : (T)~(T)0;
-    __syncthreads();
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        // pair p: i = the p-th index with bit j clear, partner i + j
-        for (uint32_t p = tid; p < (P >> 1); p += kQsSortThreads) {
-          const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-          const uint32_t l = i + j;
-          const T x = buf[i], y = buf[l];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) { buf[i] = y; buf[l] = x; }
-        }
-        __syncthreads();
-      }
-    }
-    for (uint32_t i = tid; i < n; i += kQsSortThreads) keys[q.lo + i] = buf[i];
-    __syncthreads();
-  }
-}
+// Sets the shared-memory attribute of the sort kernels (once per device).
+cudaError_t qs_prepare();
 
 }  // namespace lp

@@ -132,21 +132,21 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
     if (e != cudaSuccess) return e;
     for (uint32_t k = 0; k < nslices; k++) {
       const uint32_t cnt = hjobs[k].count;
-      const dim3 grid((cnt + 255) / 256, 1);
-      qs_build_kernel<T><<<grid, 256, 0, st>>>(L.jobs + k, L.segs);
+      if ((e = launch_qs_build<T>(L.jobs + k, 1, cnt, L.segs, st)) != cudaSuccess) return e;
       cfg.launches++;
       e = launch_batched<T>(L.segs, cnt, batch_seed, L.splits, Bs, tune, cfg);
       if (e != cudaSuccess) return e;
-      qs_split_kernel<<<grid, 256, 0, st>>>(L.jobs + k, L.segs, L.splits, Bs.totals + 2, L.acc);
+      e = launch_qs_split(L.jobs + k, 1, cnt, L.segs, L.splits, Bs.totals + 2, L.acc, st);
+      if (e != cudaSuccess) return e;
       cfg.launches++;
     }
     if ((e = mark(1)) != cudaSuccess) return e;
     // the level's small subarrays (at most two per item; the count is read on the device)
     const uint64_t small_bound = open ? 2 * open : 1;
-    const dim3 sgrid((unsigned)(small_bound < 8192 ? small_bound : 8192), 1);
-    qs_small_sort_kernel<T><<<sgrid, kQsSortThreads, 0, st>>>(L.jobs);
+    e = launch_qs_small_sort<T>(L.jobs, 1, (uint32_t)(small_bound < 8192 ? small_bound : 8192),
+                                st);
+    if (e != cudaSuccess) return e;
     cfg.launches++;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
     e = cudaMemcpyAsync(hback, L.lc, sizeof(QsLevelCounts), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

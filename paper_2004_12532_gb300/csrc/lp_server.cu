@@ -250,8 +250,8 @@ cudaError_t run_width(lp_server* s, int k, uint32_t nparts, uint32_t njobs, uint
   if (tune.ctas && tune.ctas < cfg.grid) cfg.grid = tune.ctas;
   cudaError_t e = cudaSuccess;
   if (njobs > 0 && max_open > 0) {
-    const dim3 grid((unsigned)((max_open + 255) / 256), njobs);
-    lp::qs_build_kernel<T><<<grid, 256, 0, st>>>(W.jobs, W.segs);
+    if ((e = lp::launch_qs_build<T>(W.jobs, njobs, (uint32_t)max_open, W.segs, st)) != cudaSuccess)
+      return e;
     cfg.launches++;
   }
   if (nsegs > 0) {
@@ -265,17 +265,18 @@ cudaError_t run_width(lp_server* s, int k, uint32_t nparts, uint32_t njobs, uint
     // children of the sorts' items; the keys this launch streamed go to the
     // engine's total
     if (njobs > 0 && max_open > 0) {
-      const dim3 grid((unsigned)((max_open + 255) / 256), njobs);
-      lp::qs_split_kernel<<<grid, 256, 0, st>>>(W.jobs, W.segs, W.splits, W.B.totals + 2,
-                                                s->d_acc + k);
+      e = lp::launch_qs_split(W.jobs, njobs, (uint32_t)max_open, W.segs, W.splits,
+                              W.B.totals + 2, s->d_acc + k, st);
+      if (e != cudaSuccess) return e;
     } else {
       add_traffic_kernel<<<1, 1, 0, st>>>(W.B.totals + 2, s->d_acc + k);
     }
     cfg.launches++;
   }
   if (njobs > 0 && max_small > 0) {
-    const dim3 grid((unsigned)(max_small < 2048 ? max_small : 2048), njobs);
-    lp::qs_small_sort_kernel<T><<<grid, lp::kQsSortThreads, 0, st>>>(W.jobs);
+    e = lp::launch_qs_small_sort<T>(W.jobs, njobs,
+                                    (uint32_t)(max_small < 2048 ? max_small : 2048), st);
+    if (e != cudaSuccess) return e;
     cfg.launches++;
   }
   s->stats.launches += cfg.launches;
