@@ -153,6 +153,7 @@ typedef struct {
   uint32_t line_bytes;    /* line size b * 8 of the steps: 128 .. 1024 */
   uint32_t min_chunks;    /* lines per group, at least */
   uint32_t group_workers; /* groups per segment step, at most */
+  uint32_t min_chunks_residual; /* lines per group, at least, in steps after the first */
 } lp_batch_tuning;
 
 /* One-shot: copies the segment list (host) to the device and runs the batch on
@@ -222,6 +223,22 @@ lp_status lp_ctx_sort_stats(const lp_ctx *ctx, lp_sort_stats *out);
  * batched call, the second `stream`, which must be the stream of that launch. */
 lp_status lp_ctx_last_batch_keys(lp_ctx *ctx, uint64_t *keys_out);
 lp_status lp_batch_streamed_keys(lp_batch *batch, cudaStream_t stream, uint64_t *keys_out);
+
+/* Round structure of the last batched launch (same synchronisation as
+ * above): the persistent kernel works in rounds -- plan, then one Partial
+ * Partition Step for every open segment as warp tasks.  For round r <
+ * rounds: plan_ms[r] and task_ms[r] from device timestamps, tasks[r] = warp
+ * tasks of the round (groups of multi-group steps + one-group steps). */
+#define LP_MAX_ROUNDS 12
+typedef struct {
+  uint32_t rounds;
+  uint32_t pad;
+  float plan_ms[LP_MAX_ROUNDS];
+  float task_ms[LP_MAX_ROUNDS];
+  uint64_t tasks[LP_MAX_ROUNDS];
+} lp_batch_rounds;
+lp_status lp_ctx_last_batch_rounds(lp_ctx *ctx, lp_batch_rounds *out);
+lp_status lp_batch_round_stats(lp_batch *batch, cudaStream_t stream, lp_batch_rounds *out);
 
 /* ------------------------------------------------------------ serving
  * A request engine (no counterpart in the paper): partition and sort requests

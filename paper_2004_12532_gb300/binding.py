@@ -40,7 +40,7 @@ class lp_segment_u64(C.Structure):
 
 class lp_batch_tuning(C.Structure):
     _fields_ = [("ctas", C.c_uint32), ("line_bytes", C.c_uint32), ("min_chunks", C.c_uint32),
-                ("group_workers", C.c_uint32)]
+                ("group_workers", C.c_uint32), ("min_chunks_residual", C.c_uint32)]
 
 
 class lp_sort_stats(C.Structure):
@@ -73,6 +73,18 @@ class lp_server_stats(C.Structure):
                 ("budget_bytes", C.c_uint64), ("in_use_bytes", C.c_uint64),
                 ("engine_bytes", C.c_uint64), ("busy_s", C.c_double),
                 ("batched_ms", C.c_double)]
+
+
+class lp_batch_rounds(C.Structure):
+    _fields_ = [("rounds", C.c_uint32), ("pad", C.c_uint32),
+                ("plan_ms", C.c_float * 12), ("task_ms", C.c_float * 12),
+                ("tasks", C.c_uint64 * 12)]
+
+
+def _rounds_dict(r):
+    k = r.rounds
+    return [{"plan_ms": r.plan_ms[i], "task_ms": r.task_ms[i], "tasks": int(r.tasks[i])}
+            for i in range(k)]
 
 
 _SIGS = {
@@ -109,6 +121,8 @@ _SIGS = {
     "lp_ctx_sort_stats": (_i, [_p, _p]),
     "lp_ctx_last_batch_keys": (_i, [_p, _pu64]),
     "lp_batch_streamed_keys": (_i, [_p, _p, _pu64]),
+    "lp_ctx_last_batch_rounds": (_i, [_p, _p]),
+    "lp_batch_round_stats": (_i, [_p, _p, _p]),
     "lp_server_create": (_i, [_i, _p, C.POINTER(_p)]),
     "lp_server_destroy": (_i, [_p]),
     "lp_server_last_error": (C.c_char_p, [_p]),
@@ -209,6 +223,12 @@ class Ctx:
         st = lp_sort_stats()
         self.check(lib().lp_ctx_sort_stats(self.h, C.byref(st)))
         return {f: getattr(st, f) for f, _ in lp_sort_stats._fields_}
+
+    def last_batch_rounds(self):
+        """lp_ctx_last_batch_rounds: per round of the last one-shot batch."""
+        r = lp_batch_rounds()
+        self.check(lib().lp_ctx_last_batch_rounds(self.h, C.byref(r)))
+        return _rounds_dict(r)
 
     def last_batch_keys(self):
         """lp_ctx_last_batch_keys: keys streamed by the last one-shot batch."""
@@ -344,6 +364,12 @@ class Batch:
     def launch(self, stream=None):
         self.ctx.check(lib().lp_batch_launch(self.h, _stream(stream)))
 
+    def round_stats(self, stream=None):
+        """lp_batch_round_stats: per round of the last launch."""
+        r = lp_batch_rounds()
+        self.ctx.check(lib().lp_batch_round_stats(self.h, _stream(stream), C.byref(r)))
+        return _rounds_dict(r)
+
     def streamed_keys(self, stream=None):
         """lp_batch_streamed_keys: keys streamed by the last launch."""
         k = C.c_uint64()
@@ -368,11 +394,12 @@ def lp_autotune_batched_u64(ctx, sizes, stream=None):
     ctx.check(lib().lp_autotune_batched_u64(ctx.h, arr, len(sizes), _stream(stream),
                                             C.byref(best)))
     return {"ctas": best.ctas, "line_bytes": best.line_bytes, "min_chunks": best.min_chunks,
-            "group_workers": best.group_workers}
+            "group_workers": best.group_workers, "min_chunks_residual": best.min_chunks_residual}
 
 
-def lp_ctx_set_batch_tuning(ctx, ctas=0, line_bytes=0, min_chunks=0, group_workers=0):
-    t = lp_batch_tuning(ctas, line_bytes, min_chunks, group_workers)
+def lp_ctx_set_batch_tuning(ctx, ctas=0, line_bytes=0, min_chunks=0, group_workers=0,
+                            min_chunks_residual=0):
+    t = lp_batch_tuning(ctas, line_bytes, min_chunks, group_workers, min_chunks_residual)
     ctx.check(lib().lp_ctx_set_batch_tuning(ctx.h, C.byref(t)))
 
 

@@ -32,6 +32,7 @@ lp::BatchTuning to_internal(const lp_batch_tuning& t) {
   b.group_workers = t.group_workers;
   b.line_bytes = t.line_bytes;
   b.min_chunks = t.min_chunks;
+  b.min_chunks_residual = t.min_chunks_residual;
   return b;
 }
 
@@ -95,6 +96,7 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
   c->err.clear();
   c->last_launches = 0;
   c->last_batch_traffic = nullptr;
+  c->last_batch_tround = nullptr;
   if (count && !d_splits) return lp_fail(c, LP_ERR_INVALID_ARG, "null d_splits");
   lp_status st = check_segments(c, segs, count);
   if (st != LP_OK) return st;
@@ -131,6 +133,7 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
   e = lp::launch_batched<uint64_t>(reinterpret_cast<lp::SegDesc*>(c->d_batch), count, seed,
                                    d_splits, B, tune, cfg);
   c->last_batch_traffic = B.totals + 2;
+  c->last_batch_tround = B.tround;
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "launch");
   return LP_OK;
@@ -251,7 +254,7 @@ lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t cou
   for (uint32_t lb : line_opts)
     for (uint32_t mc : chunk_opts)
       for (uint32_t ct : cta_opts) {
-        lp_batch_tuning t{ct, lb, mc, 0};
+        lp_batch_tuning t{ct, lb, mc, 0, 0};
         c->tuning = t;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 2 && st == LP_OK; rep++) {
@@ -361,6 +364,45 @@ lp_status lp_batch_streamed_keys(lp_batch* b, cudaStream_t stream, uint64_t* key
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "read streamed keys");
   *keys_out = c->h_pinned[0];
   return LP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+lp_status read_rounds(lp_ctx* c, const unsigned long long* d_tround, cudaStream_t st,
+                      lp_batch_rounds* out) {
+  *out = lp_batch_rounds{};
+  if (!d_tround) return LP_OK;
+  static_assert(lp::kBatchRoundSlots == LP_MAX_ROUNDS, "round slots");
+  unsigned long long w[LP_MAX_ROUNDS * 4];
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(w, d_tround, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "read round timestamps");
+  for (uint32_t r = 0; r < LP_MAX_ROUNDS; r++) {
+    const unsigned long long* x = w + 4 * r;
+    if (!x[0]) break;
+    out->rounds = r + 1;
+    if (x[1] > x[0]) out->plan_ms[r] = (float)((double)(x[1] - x[0]) * 1e-6);
+    if (x[2] > x[1] && x[1]) out->task_ms[r] = (float)((double)(x[2] - x[1]) * 1e-6);
+    out->tasks[r] = x[3];
+  }
+  return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_ctx_last_batch_rounds(lp_ctx* c, lp_batch_rounds* out) {
+  if (!c || !out) return LP_ERR_INVALID_ARG;
+  return read_rounds(c, c->last_batch_tround, c->last_stream, out);
+}
+
+lp_status lp_batch_round_stats(lp_batch* b, cudaStream_t stream, lp_batch_rounds* out) {
+  if (!b || !out) return LP_ERR_INVALID_ARG;
+  return read_rounds(b->ctx, b->count ? b->B.tround : nullptr, stream, out);
 }
 
 lp_status lp_quicksort_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,

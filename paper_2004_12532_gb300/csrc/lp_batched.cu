@@ -1,22 +1,28 @@
 // lp_batched.cu -- many independent partitions in one persistent cooperative
 // launch.  Each segment is partitioned by the Recursive Smoothed Striding
-// scheme of Sec. 4 (Partial Partition Steps on its open range [v_min, v_max))
-// and finished on chip once its open range fits one CTA's shared memory.
+// scheme of Sec. 4: Partial Partition Steps on its open range [v_min, v_max)
+// until the range is empty.
 //
 // The kernel works in rounds, with grid barriers between phases:
-//   plan  (CTA 0): for every open segment, the last step's v_min / v_max
-//         become the new open range; a range one CTA can hold becomes a CTA
-//         task, a larger one gets a step (line size b, g groups) from the
-//         parameter rule; group counts are prefix-summed into a task list;
-//   warp  every warp takes (segment, group) tasks from an atomic counter and
-//         partitions that group (warp_pair_group, as in the single partition);
-//         v_i go to the segment's record by atomic min / max;
-//   cta   every CTA takes CTA tasks from an atomic counter: the open range is
-//         partitioned in shared memory and the unaligned head and tail keys
-//         of the segment are put in place; the split is written.
-// The result of every segment is the partition the single-array entry points
-// produce for it (same kernels per group, same on-chip finish); only the
-// interleaving of work differs.
+//   plan  every CTA takes a slice of the segments: the last step's v_min /
+//         v_max become the open range; an empty range finishes the segment
+//         (its unaligned head and tail are put in place, the split written);
+//         a residual range (after the first step) that one CTA's shared
+//         memory holds becomes a CTA task (the base case, finished on chip);
+//         a first range of at most warp_cap keys gets a one-group step (g = 1:
+//         one warp partitions the whole range, as the paper's base case
+//         partitions serially); a larger one a step with g groups from the
+//         parameter rule.  Grid barrier; every CTA places its slice's tasks:
+//         CTA tasks and one-group segments in lists, multi-group segments
+//         with the prefix of their group counts.  Grid barrier.
+//   tasks every CTA takes CTA tasks from one counter; then every warp takes
+//         warp tasks from another -- the groups of multi-group segments first
+//         (binary search over their prefix), then the one-group segments --
+//         and partitions that group (warp_pair_group, as in the single
+//         partition); v_i go to the segment's record by atomic min / max.
+//         Grid barrier.
+// A segment's steps depend on its own size and state only (never on what it
+// is batched with), so its result is the same in any batch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,7 +34,7 @@ namespace lp {
 
 namespace {
 
-enum : uint32_t { kSegOpen = 0, kSegCta = 1, kSegDone = 2 };
+enum : uint32_t { kSegOpen = 0, kSegDone = 2 };
 
 // Segment fields written by other CTAs are read through L2, never from L1.
 __device__ __forceinline__ uint64_t L2(const uint64_t& x) {
@@ -86,174 +92,213 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   using R = Tr<T, false>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ unsigned int flag;
+  __shared__ uint32_t wsum[4][R::Warps];
+  __shared__ uint32_t base_s[4];
+  __shared__ unsigned long long tot_s[4];
   __shared__ uint32_t fetch;
-  __shared__ unsigned long long tot_s[2];
+  const uint32_t cta_cap = Coop<T, false>::Keys;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
   WarpSmem<T, false>& ws = reinterpret_cast<WarpSmem<T, false>*>(smem_raw)[warp];
   uint32_t phase = 0;
-  const uint64_t total_warps = (uint64_t)gridDim.x * R::Warps;
-  const uint32_t cta_cap = Coop<T, false>::Keys;
   TaskScratch S;
   S.status = B.status;
   S.bar = B.bar;
+  // this CTA's slice of the segments
+  const uint32_t s_lo = (uint32_t)((uint64_t)count * blockIdx.x / gridDim.x);
+  const uint32_t s_hi = (uint32_t)((uint64_t)count * (blockIdx.x + 1) / gridDim.x);
+  if (lane == 0) {
+    for (uint32_t st = 0; st < kStages; st++) mbar_init(&ws.bar[st], 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  __syncwarp();
 
-  // one round more than levels: the last forced step still gets its final plan
+  // CTA-wide exclusive scan of (single, groups, multi, cta) over the slice
+  // in chunks of R::Threads; this thread's offsets and the chunk totals
+  auto cta_scan = [&](const uint32_t (&in)[4], uint32_t (&ex)[4], uint32_t (&tot)[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      uint32_t v = in[c];
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      if (lane == 31) wsum[c][warp] = v;
+      ex[c] = v - in[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      uint32_t before = 0, all = 0;
+      for (uint32_t w = 0; w < R::Warps; w++) {
+        const uint32_t y = wsum[c][w];
+        if (w < warp) before += y;
+        all += y;
+      }
+      ex[c] += before;
+      tot[c] = all;
+    }
+    __syncthreads();
+  };
+
+  const bool stamp = blockIdx.x == 0 && tid == 0;
   for (uint32_t round = 0; round <= a.max_rounds; round++) {
-    // ------------------------------------------------------------ plan
-    if (blockIdx.x == 0) {
-      unsigned long long wrun = 0, crun = 0;  // running totals of earlier chunks
-      for (uint32_t c0 = 0; c0 < count; c0 += R::Threads) {
-        const uint32_t s = c0 + tid;
-        uint32_t gw = 0, gc = 0;
-        if (s < count) {
-          SegDesc& d = segs[s];
-          const uint32_t level = L2(d.level);
-          if (L2(d.state) == kSegOpen) {
-            const uint64_t h = L2(d.h), be = L2(d.be);
-            uint64_t lo = L2(d.lo), hi = L2(d.hi);
-            if (level > 0) {  // the step of the last round left [vmin, vmax)
-              lo = L2(d.vmin);
-              hi = L2(d.vmax);
-              if (level == 1) d.body_count = L2(d.count);
-              if (lo < hi) {  // to the 16-byte grid of the body
-                lo = h + ((lo - h) / R::A) * R::A;
-                const uint64_t h2 = h + ((hi - h + R::A - 1) / R::A) * R::A;
-                hi = h2 < be ? h2 : be;
-              }
+    unsigned long long* tr = round < kBatchRoundSlots ? B.tround + 4 * round : nullptr;
+    if (stamp && tr) tr[0] = global_timer_ns();
+    // ------------------------------------------------------------ plan A
+    uint32_t my[4] = {0, 0, 0, 0};  // singles, multi groups, multi segments, CTA tasks
+    for (uint32_t c0 = s_lo; c0 < s_hi; c0 += R::Threads) {
+      const uint32_t s = c0 + tid;
+      uint32_t in[4] = {0, 0, 0, 0};
+      if (s < s_hi) {
+        SegDesc& d = segs[s];
+        if (L2(d.state) == kSegOpen) {
+          const uint32_t level = L2(d.level);  // steps issued so far
+          const uint64_t h = L2(d.h), be = L2(d.be), n = L2(d.n);
+          uint64_t lo = L2(d.lo), hi = L2(d.hi);
+          if (level > 0) {  // the last step left [vmin, vmax)
+            lo = L2(d.vmin);
+            hi = L2(d.vmax);
+            if (level == 1) d.body_count = L2(d.count);
+            if (lo < hi) {  // to the 16-byte grid of the body
+              lo = h + ((lo - h) / R::A) * R::A;
+              const uint64_t h2 = h + ((hi - h + R::A - 1) / R::A) * R::A;
+              hi = h2 < be ? h2 : be;
+            } else {
+              lo = hi = 0;
             }
+          }
+          const uint64_t m = hi > lo ? hi - lo : 0;
+          if (m == 0) {  // finished: head and tail, then the split
+            const unsigned long long t = seg_fixup<T>(
+                reinterpret_cast<T*>(d.keys), n, h, be,
+                level > 0 ? (unsigned long long)L2(d.body_count) : 0ull, (T)L2(d.pivot));
+            d.t = t;
+            a.splits[s] = t;
+            d.state = kSegDone;
+          } else {
             d.lo = lo;
             d.hi = hi;
-            const uint64_t m = hi > lo ? hi - lo : 0;
-            const uint64_t n = L2(d.n);
-            if (m == 0 && level > 0) {
-              const unsigned long long t = seg_fixup<T>(
-                  reinterpret_cast<T*>(d.keys), n, h, be, L2(d.body_count), (T)L2(d.pivot));
-              d.t = t;
-              a.splits[s] = t;
-              d.state = kSegDone;
-            } else if ((level == 0 && n <= cta_cap) || (level > 0 && m <= cta_cap)) {
-              d.state = kSegCta;
-              gc = 1;
-              atomicAdd(&B.totals[2], (unsigned long long)(level == 0 ? n : m));
+            atomicAdd(&B.totals[2], (unsigned long long)m);  // keys this round streams
+            if (level > 0 && m <= cta_cap) {
+              d.g = 0;  // a CTA task
+              in[3] = 1;
             } else {
-              atomicAdd(&B.totals[2], (unsigned long long)m);
-              const StepParams P =
-                  choose_params(m, R::K, a.group_workers, a.line_bytes, a.min_chunks);
+              StepParams P = choose_params(m, R::K, a.group_workers, a.line_bytes,
+                                           level ? a.min_chunks_residual : a.min_chunks);
+              if (m <= a.warp_cap || level + 1 >= a.max_rounds) P.g = 1;
               d.b = P.b;
-              d.g = (level + 1 >= a.max_rounds) ? 1 : P.g;
+              d.g = P.g;
               d.vmin = ~0ull;
               d.vmax = 0ull;
               d.count = 0ull;
-              gw = (uint32_t)d.g;
+              d.level = level + 1;
+              if (P.g == 1) in[0] = 1;
+              else { in[1] = (uint32_t)P.g; in[2] = 1; }
             }
           }
         }
-        // CTA-wide exclusive scans of gw and gc
-        uint32_t iw = gw, ic = gc;
+      }
+      uint32_t ex[4], tot[4];
+      cta_scan(in, ex, tot);
 #pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-          const uint32_t x = __shfl_up_sync(0xffffffffu, iw, o);
-          const uint32_t y = __shfl_up_sync(0xffffffffu, ic, o);
-          if (lane >= o) { iw += x; ic += y; }
+      for (int c = 0; c < 4; c++) my[c] += tot[c];
+    }
+    if (tid < 4) B.cta_tot[4 * blockIdx.x + tid] = my[tid];
+    if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+
+    // ------------------------------------------------------------ plan B
+    // this CTA's offsets: the totals of the CTAs before it; and the grand totals
+    {
+      uint32_t before[4] = {0, 0, 0, 0}, all[4] = {0, 0, 0, 0};
+      for (uint32_t c = tid; c < gridDim.x; c += R::Threads) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const uint32_t y = __ldcg(&B.cta_tot[4 * c + q]);
+          if (c < blockIdx.x) before[q] += y;
+          all[q] += y;
         }
-        uint32_t* wsw = reinterpret_cast<uint32_t*>(smem_raw);  // plan scratch (CTA 0)
-        if (lane == 31) { wsw[warp] = iw; wsw[32 + warp] = ic; }
-        __syncthreads();
-        uint32_t bw = 0, bc = 0, tw = 0, tc = 0;
-        for (uint32_t w = 0; w < R::Warps; w++) {
-          const uint32_t x = wsw[w], y = wsw[32 + w];
-          if (w < warp) { bw += x; bc += y; }
-          tw += x;
-          tc += y;
-        }
-        if (s < count) {
-          B.wprefix[s] = wrun + bw + iw - gw;
-          if (gc) B.ctalist[crun + bc + ic - gc] = s;
-        }
-        wrun += tw;
-        crun += tc;
-        __syncthreads();
       }
-      if (tid == 0) {
-        B.wprefix[count] = wrun;
-        B.totals[0] = wrun;
-        B.totals[1] = crun;
-        B.counters[0] = 0u;
-        B.counters[1] = 0u;
-        __threadfence();
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+#pragma unroll
+        for (uint32_t o = 16; o > 0; o >>= 1) {
+          before[q] += __shfl_xor_sync(0xffffffffu, before[q], o);
+          all[q] += __shfl_xor_sync(0xffffffffu, all[q], o);
+        }
+        if (lane == 0) wsum[q][warp] = before[q];
       }
+      __syncthreads();
+      if (tid < 4) {
+        uint32_t b = 0;
+        for (uint32_t w = 0; w < R::Warps; w++) b += wsum[tid][w];
+        base_s[tid] = b;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (lane == 0) wsum[q][warp] = all[q];
+      __syncthreads();
+      if (tid < 4) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < R::Warps; w++) t += wsum[tid][w];
+        tot_s[tid] = t;
+      }
+      __syncthreads();
+    }
+    uint32_t run[4] = {base_s[0], base_s[1], base_s[2], base_s[3]};
+    for (uint32_t c0 = s_lo; c0 < s_hi; c0 += R::Threads) {
+      const uint32_t s = c0 + tid;
+      uint32_t in[4] = {0, 0, 0, 0};
+      if (s < s_hi && L2(segs[s].state) == kSegOpen) {
+        const uint64_t g = L2(segs[s].g);
+        if (g == 0) in[3] = 1;
+        else if (g == 1) in[0] = 1;
+        else { in[1] = (uint32_t)g; in[2] = 1; }
+      }
+      uint32_t ex[4], tot[4];
+      cta_scan(in, ex, tot);
+      if (in[0]) B.singles[run[0] + ex[0]] = s;
+      if (in[2]) {
+        B.mprefix[run[2] + ex[2]] = run[1] + ex[1];
+        B.mseg[run[2] + ex[2]] = s;
+      }
+      if (in[3]) B.ctalist[run[3] + ex[3]] = s;
+#pragma unroll
+      for (int c = 0; c < 4; c++) run[c] += tot[c];
+    }
+    const unsigned long long n_single = tot_s[0], w_multi = tot_s[1];
+    const uint32_t n_multi = (uint32_t)tot_s[2], n_cta = (uint32_t)tot_s[3];
+    if (blockIdx.x == 0 && tid == 0) {
+      B.mprefix[n_multi] = w_multi;
+      B.counters[0] = 0u;
+      B.counters[1] = 0u;
+      __threadfence();
     }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
-    if (tid == 0) {
-      tot_s[0] = __ldcg(&B.totals[0]);
-      tot_s[1] = __ldcg(&B.totals[1]);
-    }
-    __syncthreads();
-    const uint64_t W = tot_s[0], Cn = tot_s[1];
-    if (W == 0 && Cn == 0) break;  // every segment is done
+    if (n_single == 0 && w_multi == 0 && n_cta == 0) break;  // every segment is done
 
-    // ------------------------------------------------------------ warp tasks
-    if (W > 0) {
-      if (lane == 0) {
-        for (uint32_t st = 0; st < kStages; st++) mbar_init(&ws.bar[st], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();
-      }
-      __syncwarp();
-      phase = 0;
-      for (;;) {
-        uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&B.counters[0], 1u);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= W) break;
-        // segment of task k: the last s with wprefix[s] <= k
-        uint32_t lo_s = 0, hi_s = count;
-        while (hi_s - lo_s > 1) {
-          const uint32_t mid = (lo_s + hi_s) >> 1;
-          if (__ldcg(&B.wprefix[mid]) <= k) lo_s = mid; else hi_s = mid;
-        }
-        const uint32_t s = lo_s;
-        SegDesc& d = segs[s];
-        const uint64_t i = k - __ldcg(&B.wprefix[s]);
-        const uint64_t lo = L2(d.lo), hi = L2(d.hi);
-        const uint64_t b = L2(d.b), g = L2(d.g);
-        const uint32_t lev = L2(d.level);
-        const StepGeom G = make_geom(hi - lo, b, g, level_seed(L2(d.seed), lev), 0);
-        T* base = reinterpret_cast<T*>(d.keys) + lo;
-        const int32_t nl = (int32_t)group_num_lines(G, i);
-        uint64_t kk = 0;
-        if (!warp_pair_group<T, false>(base, nullptr, G, (uint32_t)i, nl, (T)L2(d.pivot), ws,
-                                       phase, kk, S.status))
-          break;
-        if (nl > 0 && lane == 0) {
-          const unsigned long long v = lo + group_split_pos(G, i, (uint64_t)nl, kk);
-          atomicMin(&d.vmin, v);
-          atomicMax(&d.vmax, v);
-          atomicAdd(&d.count, (unsigned long long)kk);
-        }
-      }
-      __syncwarp();
-      if (lane == 0)  // the CTA tasks reuse this shared memory
+    // ------------------------------------------------------------ tasks
+    const unsigned long long W = w_multi + n_single;
+    if (stamp && tr) {
+      tr[1] = global_timer_ns();
+      tr[3] = W + n_cta;
+    }
+    if (n_cta > 0) {  // CTA tasks first: they use the warps' shared memory
+      if (lane == 0)
         for (uint32_t st = 0; st < kStages; st++) mbar_inval(&ws.bar[st]);
-    }
-    if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
-
-    // ------------------------------------------------------------ CTA tasks
-    for (;;) {
-      if (tid == 0) fetch = atomicAdd(&B.counters[1], 1u);
       __syncthreads();
-      const uint32_t c = fetch;
-      __syncthreads();
-      if (c >= Cn) break;
-      const uint32_t s = __ldcg(&B.ctalist[c]);
-      SegDesc& d = segs[s];
-      T* keys = reinterpret_cast<T*>(d.keys);
-      const T pivot = (T)L2(d.pivot);
-      if (L2(d.level) == 0) {  // the whole segment, any alignment
-        const uint32_t cnt = cta_partition_smem<T, false>(keys, nullptr, (uint32_t)L2(d.n),
-                                                          pivot, smem_raw);
-        if (tid == 0) { d.t = cnt; a.splits[s] = cnt; d.state = kSegDone; }
-      } else {  // the open range of the body, then the head and tail
+      for (;;) {
+        if (tid == 0) fetch = atomicAdd(&B.counters[1], 1u);
+        __syncthreads();
+        const uint32_t c = fetch;
+        __syncthreads();
+        if (c >= n_cta) break;
+        const uint32_t s = __ldcg(&B.ctalist[c]);
+        SegDesc& d = segs[s];
+        T* keys = reinterpret_cast<T*>(d.keys);
+        const T pivot = (T)L2(d.pivot);
         const uint64_t lo = L2(d.lo), hi = L2(d.hi);
         cta_partition_smem<T, false>(keys + lo, nullptr, (uint32_t)(hi - lo), pivot, smem_raw);
         if (tid == 0) {
@@ -264,24 +309,67 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
           a.splits[s] = t;
           d.state = kSegDone;
         }
+        __syncthreads();
       }
-      __syncthreads();
+      if (lane == 0) {
+        for (uint32_t st = 0; st < kStages; st++) mbar_init(&ws.bar[st], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+      }
+      __syncwarp();
+      phase = 0;
     }
-    // segments that took a step move to the next level
-    if (blockIdx.x == 0) {
-      for (uint32_t s = tid; s < count; s += R::Threads)
-        if (L2(segs[s].state) == kSegOpen) segs[s].level = L2(segs[s].level) + 1;
+    for (;;) {
+      uint32_t k = 0;
+      if (lane == 0) k = atomicAdd(&B.counters[0], 1u);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      if (k >= W) break;
+      uint32_t s, i;
+      if (k < w_multi) {  // a group of a multi-group segment: the last entry <= k
+        uint32_t lo_s = 0, hi_s = n_multi;
+        while (hi_s - lo_s > 1) {
+          const uint32_t mid = (lo_s + hi_s) >> 1;
+          if (__ldcg(&B.mprefix[mid]) <= k) lo_s = mid; else hi_s = mid;
+        }
+        s = __ldcg(&B.mseg[lo_s]);
+        i = (uint32_t)(k - __ldcg(&B.mprefix[lo_s]));
+      } else {
+        s = __ldcg(&B.singles[k - w_multi]);
+        i = 0;
+      }
+      SegDesc& d = segs[s];
+      const uint64_t lo = L2(d.lo), hi = L2(d.hi);
+      const uint64_t b = L2(d.b), g = L2(d.g);
+      const uint32_t lev = L2(d.level);
+      const StepGeom G = make_geom(hi - lo, b, g, level_seed(L2(d.seed), lev), 0);
+      T* base = reinterpret_cast<T*>(d.keys) + lo;
+      const int32_t nl = (int32_t)group_num_lines(G, i);
+      uint64_t kk = 0;
+      if (!warp_pair_group<T, false>(base, nullptr, G, i, nl, (T)L2(d.pivot), ws, phase, kk,
+                                     S.status))
+        break;
+      if (nl > 0 && lane == 0) {
+        const unsigned long long v = lo + group_split_pos(G, i, (uint64_t)nl, kk);
+        atomicMin(&d.vmin, v);
+        atomicMax(&d.vmax, v);
+        atomicAdd(&d.count, (unsigned long long)kk);
+      }
     }
+    __syncwarp();
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+    if (stamp && tr) tr[2] = global_timer_ns();
   }
+  if (lane == 0)
+    for (uint32_t st = 0; st < kStages; st++) mbar_inval(&ws.bar[st]);
 }
 
 // Per-segment set-up on the device: the 16-byte aligned body of each segment.
 template <typename T>
 __global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed,
-                                   unsigned long long* traffic) {
+                                   unsigned long long* traffic, unsigned long long* tround) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) *traffic = 0ull;
+  if (s < kBatchRoundSlots * 4) tround[s] = 0ull;
   if (s >= count) return;
   SegDesc& d = segs[s];
   constexpr uint32_t K = sizeof(T), A = 16 / sizeof(T);
@@ -306,17 +394,30 @@ __global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed,
 
 }  // namespace
 
+namespace {
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
 size_t batch_scratch_bytes(uint32_t count) {
-  return (((size_t)count + 1) * 8 + 255) / 256 * 256 + ((size_t)count * 4 + 255) / 256 * 256 + 256;
+  return up256(((size_t)count + 1) * 8) + 3 * up256((size_t)count * 4) +
+         up256((size_t)kBatchMaxGrid * 4 * 4) + up256(kBatchRoundSlots * 4 * 8) + 256;
 }
 
 BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint32_t* status) {
   unsigned char* p = static_cast<unsigned char*>(base);
   BatchScratch B;
-  B.wprefix = reinterpret_cast<unsigned long long*>(p);
-  p += (((size_t)count + 1) * 8 + 255) / 256 * 256;
+  B.mprefix = reinterpret_cast<unsigned long long*>(p);
+  p += up256(((size_t)count + 1) * 8);
+  B.mseg = reinterpret_cast<uint32_t*>(p);
+  p += up256((size_t)count * 4);
+  B.singles = reinterpret_cast<uint32_t*>(p);
+  p += up256((size_t)count * 4);
   B.ctalist = reinterpret_cast<uint32_t*>(p);
-  p += ((size_t)count * 4 + 255) / 256 * 256;
+  p += up256((size_t)count * 4);
+  B.cta_tot = reinterpret_cast<uint32_t*>(p);
+  p += up256((size_t)kBatchMaxGrid * 4 * 4);
+  B.tround = reinterpret_cast<unsigned long long*>(p);
+  p += up256(kBatchRoundSlots * 4 * 8);
   B.totals = reinterpret_cast<unsigned long long*>(p);
   B.counters = reinterpret_cast<uint32_t*>(p + 64);
   B.bar = bar;
@@ -330,8 +431,9 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   using R = Tr<T, false>;
   cudaStream_t st = cfg.stream;
   if (count == 0) return cudaSuccess;
-  batch_setup_kernel<T><<<(count + 255) / 256, 256, 0, st>>>(d_segs, count, seed,
-                                                              Bs.totals + 2);
+  const uint32_t setup_threads = count > kBatchRoundSlots * 4 ? count : kBatchRoundSlots * 4;
+  batch_setup_kernel<T><<<(setup_threads + 255) / 256, 256, 0, st>>>(d_segs, count, seed,
+                                                                      Bs.totals + 2, Bs.tround);
   cfg.launches++;
   cudaError_t e = cudaMemsetAsync(Bs.bar, 0, 8, st);
   if (e != cudaSuccess) return e;
@@ -342,9 +444,12 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   a.max_rounds = kMaxLevels;
   uint32_t grid = cfg.grid;
   if (tune.ctas && tune.ctas < grid) grid = tune.ctas;
+  if (grid > kBatchMaxGrid) grid = kBatchMaxGrid;
   a.group_workers = tune.group_workers ? tune.group_workers : (uint64_t)grid * R::Warps;
   a.line_bytes = tune.line_bytes ? tune.line_bytes : R::LineBytes;
   a.min_chunks = tune.min_chunks ? tune.min_chunks : 64;
+  a.warp_cap = kWarpCapBytes / R::K;
+  a.min_chunks_residual = tune.min_chunks_residual ? tune.min_chunks_residual : a.min_chunks;
   const size_t smem = level_smem_bytes<T, false>();  // attribute set by batched_prepare
   e = launch_cooperative(batched_kernel<T>, grid, R::Threads, smem, st, d_segs, count, a, Bs);
   cfg.launches++;

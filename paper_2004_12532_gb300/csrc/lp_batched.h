@@ -26,19 +26,33 @@ struct SegDesc {
   uint32_t level, state;
 };
 
+// Open ranges of at most this many bytes get a one-group step: one warp
+// partitions the whole range.
+constexpr uint32_t kWarpCapBytes = 128u * 1024u;
+// CTAs of a batched launch, at most (plan space per CTA)
+constexpr uint32_t kBatchMaxGrid = 1024;
+// rounds recorded in BatchScratch::tround
+constexpr uint32_t kBatchRoundSlots = 12;
+
 struct BatchArgs {
   uint64_t* splits;       // one split per segment (device)
   uint32_t max_rounds;
   uint64_t group_workers; // at most this many groups per segment step
   uint32_t line_bytes;    // line size of the steps
   uint32_t min_chunks;    // lines per group, at least
+  uint64_t warp_cap;      // one-group steps for open ranges of at most this many keys
+  uint32_t min_chunks_residual;  // lines per group, at least, after the first step
 };
 
 struct BatchScratch {
-  unsigned long long* wprefix;  // count + 1 task prefix entries
-  uint32_t* ctalist;            // count CTA-task segment ids
-  unsigned long long* totals;   // warp tasks, CTA tasks of the round; keys streamed
-  uint32_t* counters;           // task fetch counters
+  unsigned long long* mprefix;  // multi-group segments: prefix of their group counts
+  uint32_t* mseg;               // multi-group segments: ids
+  uint32_t* singles;            // one-group segments: ids
+  uint32_t* ctalist;            // CTA-task segments: ids
+  uint32_t* cta_tot;            // per CTA: singles, groups, multi-group segments, CTA tasks
+  unsigned long long* totals;   // [2]: keys streamed
+  unsigned long long* tround;   // per round: plan start, tasks start, tasks end (ns), tasks
+  uint32_t* counters;           // task fetch counter
   uint32_t* bar;                // grid barrier
   uint32_t* status;
 };
@@ -49,6 +63,7 @@ struct BatchTuning {
   uint64_t group_workers;  // groups per segment step, at most
   uint32_t line_bytes;     // 128..1024
   uint32_t min_chunks;     // lines per group, at least
+  uint32_t min_chunks_residual;  // ... in steps after the first
 };
 
 size_t batch_scratch_bytes(uint32_t count);

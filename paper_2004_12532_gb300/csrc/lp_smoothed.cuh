@@ -370,12 +370,30 @@ __device__ uint32_t cta_partition_smem(T* __restrict__ keys, uint64_t* __restric
   uint64_t* sv = reinterpret_cast<uint64_t*>(
       smem + 128 + (((size_t)n * sizeof(T) + 15) & ~size_t(15)));
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  for (uint32_t q = tid; q < n; q += NT) {  // through L2: other CTAs may have written these
-    if constexpr (sizeof(T) == 8)
-      sk[q] = (T)__ldcg(reinterpret_cast<const unsigned long long*>(keys + q));
-    else
-      sk[q] = (T)__ldcg(reinterpret_cast<const unsigned int*>(keys + q));
-    if constexpr (KV) sv[q] = __ldcg(reinterpret_cast<const unsigned long long*>(vals + q));
+  // through L2 (other CTAs may have written these), 8 loads in flight per thread
+  constexpr uint32_t U = 8;
+  for (uint32_t q0 = tid; q0 < n; q0 += NT * U) {
+    T x[U];
+    uint64_t y[KV ? U : 1];
+#pragma unroll
+    for (uint32_t u = 0; u < U; u++) {
+      const uint32_t q = q0 + u * NT;
+      if (q < n) {
+        if constexpr (sizeof(T) == 8)
+          x[u] = (T)__ldcg(reinterpret_cast<const unsigned long long*>(keys + q));
+        else
+          x[u] = (T)__ldcg(reinterpret_cast<const unsigned int*>(keys + q));
+        if constexpr (KV) y[u] = __ldcg(reinterpret_cast<const unsigned long long*>(vals + q));
+      }
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; u++) {
+      const uint32_t q = q0 + u * NT;
+      if (q < n) {
+        sk[q] = x[u];
+        if constexpr (KV) sv[q] = y[u];
+      }
+    }
   }
   __syncthreads();
   const uint32_t per = (n + NT - 1) / NT;
