@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   __shared__ uint32_t base_s[4];
   __shared__ unsigned long long tot_s[4];
   __shared__ uint32_t fetch;
-  const uint32_t cta_cap = Coop<T, false>::Keys;
+  __shared__ __align__(8) uint64_t cta_bar;  // the CTA tasks' bulk copies
+  uint32_t cta_parity = 0;
+  const uint32_t cta_cap = CtaBulk<T>::Keys;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
   WarpSmem<T, false>& ws = reinterpret_cast<WarpSmem<T, false>*>(smem_raw)[warp];
   uint32_t phase = 0;
@@ -108,10 +110,11 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   const uint32_t s_hi = (uint32_t)((uint64_t)count * (blockIdx.x + 1) / gridDim.x);
   if (lane == 0) {
     for (uint32_t st = 0; st < kStages; st++) mbar_init(&ws.bar[st], 1);
+    if (tid == 0) mbar_init(&cta_bar, 1);
     fence_mbar_init();
     fence_proxy_async_smem();
   }
-  __syncwarp();
+  __syncthreads();
 
   // CTA-wide exclusive scan of (single, groups, multi, cta) over the slice
   // in chunks of R::Threads; this thread's offsets and the chunk totals
@@ -182,7 +185,10 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
             d.hi = hi;
             atomicAdd(&B.totals[2], (unsigned long long)m);  // keys this round streams
             if (level > 0 && m <= cta_cap) {
-              d.g = 0;  // a CTA task
+              // a residual range one CTA holds: finished on chip (a CTA task);
+              // first ranges that small stay one-warp steps, which many
+              // small segments keep busy in parallel
+              d.g = 0;
               in[3] = 1;
             } else {
               StepParams P = choose_params(m, R::K, a.group_workers, a.line_bytes,
@@ -300,11 +306,14 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
         T* keys = reinterpret_cast<T*>(d.keys);
         const T pivot = (T)L2(d.pivot);
         const uint64_t lo = L2(d.lo), hi = L2(d.hi);
-        cta_partition_smem<T, false>(keys + lo, nullptr, (uint32_t)(hi - lo), pivot, smem_raw);
+        const uint32_t cnt = cta_partition_bulk<T>(keys + lo, (uint32_t)(hi - lo), pivot,
+                                                   smem_raw, &cta_bar, cta_parity, S.status);
+        if (cnt == ~0u) break;  // a wait gave up (status set)
         if (tid == 0) {
           __threadfence_block();
-          const unsigned long long t =
-              seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), L2(d.body_count), pivot);
+          // a first-level CTA task partitioned the whole body
+          const unsigned long long bc = L2(d.level) == 0 ? cnt : L2(d.body_count);
+          const unsigned long long t = seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), bc, pivot);
           d.t = t;
           a.splits[s] = t;
           d.state = kSegDone;
@@ -359,8 +368,11 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
     if (stamp && tr) tr[2] = global_timer_ns();
   }
-  if (lane == 0)
+  __syncthreads();
+  if (lane == 0) {
     for (uint32_t st = 0; st < kStages; st++) mbar_inval(&ws.bar[st]);
+    if (tid == 0) mbar_inval(&cta_bar);
+  }
 }
 
 // Per-segment set-up on the device: the 16-byte aligned body of each segment.

@@ -425,4 +425,87 @@ __device__ uint32_t cta_partition_smem(T* __restrict__ keys, uint64_t* __restric
   return tot;
 }
 
+// One CTA partitions keys[0..n) in place, n * sizeof(T) a multiple of 16 and
+// keys 16-byte aligned: one bulk asynchronous copy (TMA) stages the range in
+// shared memory; predecessors are ranked by warp ballots in index order (a
+// count pass, a scan of the per-(chunk, warp) counts, a scatter pass), which
+// makes the partition stable; the stores of a warp fall in at most two runs.
+// Returns the predecessor count, or ~0u if the copy's wait gave up (status
+// set).  `bar` is a CTA-wide mbarrier (count 1) and `parity` its phase.
+template <typename T>
+struct CtaBulk {
+  static constexpr uint32_t Head = 4096;  // per-(chunk, warp) counts
+  static constexpr uint32_t Keys =
+      (uint32_t)((level_smem_bytes<T, false>() - Head) / sizeof(T)) / Tr<T, false>::A *
+      Tr<T, false>::A;
+};
+
+template <typename T>
+__device__ uint32_t cta_partition_bulk(T* __restrict__ keys, uint32_t n, T pivot,
+                                       unsigned char* smem, uint64_t* bar, uint32_t& parity,
+                                       uint32_t* status) {
+  constexpr uint32_t NT = Tr<T, false>::Threads, W = NT / 32;
+  constexpr uint32_t FULL = 0xffffffffu;
+  static_assert(((CtaBulk<T>::Keys + NT - 1) / NT) * W * 4 + 4 <= CtaBulk<T>::Head,
+                "count space");
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+  T* sk = reinterpret_cast<T*>(smem + CtaBulk<T>::Head);
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t bytes = n * (uint32_t)sizeof(T);
+  if (tid == 0) {
+    fence_proxy_async_smem();  // this shared memory was last written by threads
+    mbar_arrive_expect_tx(bar, bytes);
+    for (uint32_t off = 0; off < bytes; off += 16384u) {
+      const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
+      bulk_load(reinterpret_cast<unsigned char*>(sk) + off,
+                reinterpret_cast<const unsigned char*>(keys) + off, len, bar);
+    }
+  }
+  const bool ok = mbar_wait_bounded(bar, parity);
+  if (!ok) {
+    if (tid == 0) atomicOr(status, kStatTimeout);
+    mbar_wait_bounded(bar, parity);  // let the copy land before the memory is reused
+    __syncthreads();
+    return ~0u;
+  }
+  parity ^= 1u;
+  const uint32_t nch = (n + NT - 1) / NT;
+  for (uint32_t c = 0; c < nch; c++) {
+    const uint32_t q = c * NT + tid;
+    const bool f = q < n && sk[q] <= pivot;
+    const uint32_t bal = __ballot_sync(FULL, f);
+    if (lane == 0) cnt[c * W + warp] = __popc(bal);
+  }
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the counts in (chunk, warp) order
+    const uint32_t m = nch * W;
+    uint32_t run = 0;
+    for (uint32_t b0 = 0; b0 < m; b0 += 32) {
+      const uint32_t v = b0 + lane < m ? cnt[b0 + lane] : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (b0 + lane < m) cnt[b0 + lane] = run + incl - v;
+      run += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) cnt[(CtaBulk<T>::Head / 4) - 1] = run;
+  }
+  __syncthreads();
+  const uint32_t total = cnt[(CtaBulk<T>::Head / 4) - 1];
+  for (uint32_t c = 0; c < nch; c++) {
+    const uint32_t q = c * NT + tid;
+    const T x = q < n ? sk[q] : pivot;
+    const bool f = q < n && x <= pivot;
+    const uint32_t bal = __ballot_sync(FULL, f);
+    const uint32_t pre = cnt[c * W + warp] + __popc(bal & lt);  // predecessors before q
+    if (q < n) keys[f ? pre : total + q - pre] = x;
+  }
+  __syncthreads();
+  return total;
+}
+
 }  // namespace lp

@@ -140,3 +140,42 @@ def test_autotune_and_tuned_run(ctx):
     torch.cuda.synchronize()
     check_batch(to_host(buf, np.uint64), host, offs, sizes, pivots, splits.cpu().numpy())
     lp.lp_ctx_set_batch_tuning(ctx)  # back to defaults
+
+
+def test_round_stats_and_streamed_keys(ctx):
+    """The device-side counters: every key of every segment is streamed at
+    least once, and the round record covers the launch."""
+    sizes = [5, 3000, 40000, (1 << 21) + 7, 123457, 0, 64]
+    host, offs, pivots = make_batch(sizes, 21)
+    buf = to_dev(host)
+    views = [buf[o:o + n] for o, n in zip(offs, sizes)]
+    splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+    lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=4)
+    keys = ctx.last_batch_keys()
+    rounds = ctx.last_batch_rounds()
+    assert keys >= sum(n - 16 for n in sizes if n > 16)
+    assert 1 <= len(rounds) <= 12 and rounds[0]["tasks"] > 0
+    assert all(r["plan_ms"] >= 0 and r["task_ms"] >= 0 for r in rounds)
+    check_batch(to_host(buf, np.uint64), host, offs, sizes, pivots, splits.cpu().numpy())
+    b = lp.Batch(ctx, views, pivots, splits, seed=4)
+    buf.copy_(to_dev(host))
+    b.launch()
+    assert b.streamed_keys() == keys  # same segments, same seed: the same steps
+    assert [r["tasks"] for r in b.round_stats()] == [r["tasks"] for r in rounds]
+    b.close()
+
+
+@pytest.mark.parametrize("mcr", [8, 32])
+def test_residual_tuning_keeps_results_valid(ctx, mcr):
+    sizes = [(1 << 22) + 5, 70000, 9000, 1 << 20]
+    host, offs, pivots = make_batch(sizes, 30 + mcr)
+    buf = to_dev(host)
+    views = [buf[o:o + n] for o, n in zip(offs, sizes)]
+    splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+    lp.lp_ctx_set_batch_tuning(ctx, min_chunks_residual=mcr)
+    try:
+        lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=2)
+        torch.cuda.synchronize()
+        check_batch(to_host(buf, np.uint64), host, offs, sizes, pivots, splits.cpu().numpy())
+    finally:
+        lp.lp_ctx_set_batch_tuning(ctx)
