@@ -89,6 +89,11 @@ uint32_t lp_ctx_grid(const lp_ctx *ctx);
 /* enable != 0: later partition calls on ctx record a CUDA event on their
  * stream before each partial-step kernel and after the last one. */
 lp_status lp_ctx_set_timing(lp_ctx *ctx, int enable);
+/* Waits for the last call issued on ctx (on that call's stream) and returns
+ * its device status: LP_OK, LP_ERR_TIMEOUT (a bounded device wait gave up) or
+ * LP_ERR_INTERNAL.  This is how the outcome of the _async partitions and of
+ * lp_partition_batched_u64 is learnt. */
+lp_status lp_ctx_wait(lp_ctx *ctx);
 /* Level structure of the last Smoothed / Strided partition call on ctx (the
  * recursion of Sec. 4 on [v_min, v_max)): for level L < LP_MAX_LEVELS,
  * ranges[4L..4L+3] = {lo, hi, b, g} of the range that level partitioned
@@ -172,6 +177,9 @@ lp_status lp_batch_create(lp_ctx *ctx, const lp_segment_u64 *segs, uint32_t coun
                           uint64_t seed, uint64_t *d_splits, cudaStream_t stream,
                           lp_batch **out);
 lp_status lp_batch_launch(lp_batch *batch, cudaStream_t stream);
+/* Waits for `stream` (the stream of the batch's last launch) and returns that
+ * launch's device status, as lp_ctx_wait. */
+lp_status lp_batch_wait(lp_batch *batch, cudaStream_t stream);
 lp_status lp_batch_destroy(lp_batch *batch);
 
 /* Autotuner: times candidate tunings on a synthetic batch with the given

@@ -97,6 +97,7 @@ _SIGS = {
     "lp_ctx_set_timing": (_i, [_p, _i]),
     "lp_ctx_level_stats": (_i, [_p, _pu64, C.POINTER(C.c_float), C.POINTER(_i)]),
     "lp_ctx_kernel_ms": (_i, [_p, C.POINTER(C.c_float)]),
+    "lp_ctx_wait": (_i, [_p]),
     "lp_partition_u64": (_i, [_p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
     "lp_partition_u32": (_i, [_p, _p, _u64, _u32, _i, _u64, _p, _pu64]),
     "lp_partition_kv_u64": (_i, [_p, _p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
@@ -113,6 +114,7 @@ _SIGS = {
     "lp_partition_batched_u64": (_i, [_p, _p, _u32, _u64, _p, _p]),
     "lp_batch_create": (_i, [_p, _p, _u32, _u64, _p, _p, C.POINTER(_p)]),
     "lp_batch_launch": (_i, [_p, _p]),
+    "lp_batch_wait": (_i, [_p, _p]),
     "lp_batch_destroy": (_i, [_p]),
     "lp_autotune_batched_u64": (_i, [_p, _p, _u32, _p, _p]),
     "lp_ctx_set_batch_tuning": (_i, [_p, _p]),
@@ -217,6 +219,10 @@ class Ctx:
     @property
     def aux_bytes(self):
         return int(lib().lp_ctx_aux_bytes(self.h))
+
+    def wait(self):
+        """lp_ctx_wait: finish the last call and raise on a device error."""
+        return self.check(lib().lp_ctx_wait(self.h))
 
     def sort_stats(self):
         """lp_ctx_sort_stats: what the last quicksort on this context did."""
@@ -363,6 +369,10 @@ class Batch:
 
     def launch(self, stream=None):
         self.ctx.check(lib().lp_batch_launch(self.h, _stream(stream)))
+
+    def wait(self, stream=None):
+        """lp_batch_wait: finish the last launch and raise on a device error."""
+        return self.ctx.check(lib().lp_batch_wait(self.h, _stream(stream)))
 
     def round_stats(self, stream=None):
         """lp_batch_round_stats: per round of the last launch."""

@@ -314,6 +314,17 @@ lp_status lp_ctx_set_timing(lp_ctx* c, int enable) {
   return LP_OK;
 }
 
+lp_status lp_ctx_wait(lp_ctx* c) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_pinned + 7, c->task.status, 4, cudaMemcpyDeviceToHost,
+                        c->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "wait");
+  return status_to_lp(c, (uint32_t)(c->h_pinned[7] & 0xffffffffu));
+}
+
 lp_status lp_ctx_level_stats(lp_ctx* c, uint64_t* ranges, float* ms, int* levels) {
   if (!c || !ranges || !levels) return LP_ERR_INVALID_ARG;
   cudaError_t e = cudaSetDevice(c->device);

@@ -130,6 +130,8 @@ lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32
   lp::LaunchCfg cfg{tuned_grid(c, tune, 8), stream, 0, nullptr};
   c->last_timed = false;
   c->last_stream = stream;
+  e = cudaMemsetAsync(c->task.status, 0, 4, stream);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "reset status");
   e = lp::launch_batched<uint64_t>(reinterpret_cast<lp::SegDesc*>(c->d_batch), count, seed,
                                    d_splits, B, tune, cfg);
   c->last_batch_traffic = B.totals + 2;
@@ -182,8 +184,9 @@ lp_status lp_batch_create(lp_ctx* c, const lp_segment_u64* segs, uint32_t count,
     lp::LaunchCfg cfg{grid, cap, 0, nullptr};
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t le = lp::launch_batched<uint64_t>(b->d_segs, count, seed, d_splits, b->B,
-                                                    b->tune, cfg);
+      cudaError_t le = cudaMemsetAsync(b->B.status, 0, 4, cap);  // each launch starts clean
+      if (le == cudaSuccess)
+        le = lp::launch_batched<uint64_t>(b->d_segs, count, seed, d_splits, b->B, b->tune, cfg);
       e = cudaStreamEndCapture(cap, &b->graph);
       if (le != cudaSuccess) e = le;
     }
@@ -206,6 +209,21 @@ lp_status lp_batch_launch(lp_batch* b, cudaStream_t stream) {
   if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, stream);
   if (e != cudaSuccess) return lp_cuda_fail(b->ctx, e, "graph launch");
   b->ctx->last_launches = 2;  // kernels of the graph: set-up and the persistent kernel
+  return LP_OK;
+}
+
+lp_status lp_batch_wait(lp_batch* b, cudaStream_t stream) {
+  if (!b) return LP_ERR_INVALID_ARG;
+  if (b->count == 0) return LP_OK;
+  lp_ctx* c = b->ctx;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_pinned + 7, b->B.status, 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return lp_cuda_fail(c, e, "wait");
+  const uint32_t st = (uint32_t)(c->h_pinned[7] & 0xffffffffu);
+  if (st & lp::kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (st) return lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed");
   return LP_OK;
 }
 

@@ -378,9 +378,14 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
 // Per-segment set-up on the device: the 16-byte aligned body of each segment.
 template <typename T>
 __global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed,
-                                   unsigned long long* traffic, unsigned long long* tround) {
+                                   unsigned long long* traffic, unsigned long long* tround,
+                                   uint32_t* bar) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s == 0) *traffic = 0ull;
+  if (s == 0) {
+    *traffic = 0ull;
+    bar[0] = 0u;  // the grid barrier starts clean (the status word is the caller's)
+    bar[1] = 0u;
+  }
   if (s < kBatchRoundSlots * 4) tround[s] = 0ull;
   if (s >= count) return;
   SegDesc& d = segs[s];
@@ -445,11 +450,10 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   if (count == 0) return cudaSuccess;
   const uint32_t setup_threads = count > kBatchRoundSlots * 4 ? count : kBatchRoundSlots * 4;
   batch_setup_kernel<T><<<(setup_threads + 255) / 256, 256, 0, st>>>(d_segs, count, seed,
-                                                                      Bs.totals + 2, Bs.tround);
+                                                                      Bs.totals + 2, Bs.tround,
+                                                                      Bs.bar);
   cfg.launches++;
-  cudaError_t e = cudaMemsetAsync(Bs.bar, 0, 8, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(Bs.status, 0, 4, st);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   BatchArgs a;
   a.splits = d_splits;

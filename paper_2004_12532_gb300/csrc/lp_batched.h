@@ -74,6 +74,9 @@ BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint
 template <typename T>
 cudaError_t batched_prepare(int device, uint32_t* grid);
 
+// One persistent launch over the segments.  The grid barrier is reset by the
+// launch; the status word is not (a caller resets it once per call, so a
+// failure of any launch of the call stays visible).
 template <typename T>
 cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
                            const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg);

@@ -151,6 +151,7 @@ def test_round_stats_and_streamed_keys(ctx):
     views = [buf[o:o + n] for o, n in zip(offs, sizes)]
     splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
     lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=4)
+    ctx.wait()
     keys = ctx.last_batch_keys()
     rounds = ctx.last_batch_rounds()
     assert keys >= sum(n - 16 for n in sizes if n > 16)
@@ -160,6 +161,7 @@ def test_round_stats_and_streamed_keys(ctx):
     b = lp.Batch(ctx, views, pivots, splits, seed=4)
     buf.copy_(to_dev(host))
     b.launch()
+    b.wait()
     assert b.streamed_keys() == keys  # same segments, same seed: the same steps
     assert [r["tasks"] for r in b.round_stats()] == [r["tasks"] for r in rounds]
     b.close()
