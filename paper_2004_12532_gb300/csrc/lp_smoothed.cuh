@@ -10,8 +10,9 @@
 //   * the warp holds the lowest unfinished line L and the highest unfinished
 //     line R in registers (lane l holds vectors l and 32+l of each);
 //   * the j-th successor of L and the j-th predecessor of R are swapped for
-//     j < min(#successors(L), #predecessors(R)) -- ranks come from warp
-//     ballots, the keys cross through a small shared-memory buffer;
+//     j < min(#successors(L), #predecessors(R)) -- ranks (lane by lane)
+//     come from one warp scan of per-lane counts, the keys cross through a
+//     small shared-memory buffer;
 //   * whichever line became pure (L all predecessors, R all successors) is
 //     written straight back with coalesced 16-byte stores, and the next line
 //     of that side is taken; the last line left is partitioned on its own;
@@ -251,33 +252,34 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     }
     if (!(hasL && hasR)) break;
 
-    // swap the j-th successor of L with the j-th predecessor of R
+    // swap the j-th successor of L with the j-th predecessor of R, both
+    // numbered lane by lane (slots in order within a lane): one warp scan of
+    // the per-lane counts, packed (successors of L low, predecessors of R high)
     uint32_t lkeys = 0;  // bit j: key slot j of L exists
 #pragma unroll
     for (uint32_t u = 0; u < VPL; u++)
       if ((Lr.valid >> u) & 1u) lkeys |= ((1u << V) - 1u) << (u * V);
     const uint32_t lsucc = ~Lr.pred & lkeys;
     const uint32_t rpred = Rr.pred;
-    uint32_t bl[NB], br[NB];
-    uint32_t SL = 0, PR = 0;
+    const uint32_t own = (uint32_t)__popc(lsucc) | ((uint32_t)__popc(rpred) << 16);
+    uint32_t incl = own;
 #pragma unroll
-    for (uint32_t j = 0; j < NB; j++) {
-      bl[j] = __ballot_sync(FULL, (lsucc >> j) & 1u);
-      br[j] = __ballot_sync(FULL, (rpred >> j) & 1u);
-      SL += __popc(bl[j]);
-      PR += __popc(br[j]);
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
     }
+    const uint32_t tot = __shfl_sync(FULL, incl, 31);
+    const uint32_t SL = tot & 0xffffu, PR = tot >> 16;
     const uint32_t m = min(SL, PR);
     if (m > 0) {
-      uint32_t al = 0, ar = 0;
+      const uint32_t exl = (incl - own) & 0xffffu, exr = (incl - own) >> 16;
       uint32_t rl[NB], rr[NB];
 #pragma unroll
       for (uint32_t j = 0; j < NB; j++) {
         const uint32_t u = j / V, v = j % V;
-        rl[j] = ((lsucc >> j) & 1u) ? al + __popc(bl[j] & lt) : 0xffffffffu;
-        rr[j] = ((rpred >> j) & 1u) ? ar + __popc(br[j] & lt) : 0xffffffffu;
-        al += __popc(bl[j]);
-        ar += __popc(br[j]);
+        const uint32_t below = (1u << j) - 1u;
+        rl[j] = ((lsucc >> j) & 1u) ? exl + __popc(lsucc & below) : 0xffffffffu;
+        rr[j] = ((rpred >> j) & 1u) ? exr + __popc(rpred & below) : 0xffffffffu;
         if (rl[j] < m) {
           sm.xbuf[0][rl[j]] = Lr.x[u][v];
           if constexpr (KV) sm.vxbuf[0][rl[j]] = Lr.y[u][v];
