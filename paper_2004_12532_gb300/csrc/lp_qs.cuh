@@ -25,7 +25,7 @@
 namespace lp {
 
 constexpr uint64_t kQsCut = 4096;  // subarrays this small are sorted in shared memory
-constexpr uint32_t kQsSortThreads = 512;
+constexpr uint32_t kQsSortThreads = 256;
 
 struct QsItem {
   uint64_t lo, n, pivot;  // pivot: of an equal-key item only
