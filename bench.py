@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-yardstick", action="store_true",
+                    help="skip the out-of-place library partition timed beside ours")
     ap.add_argument("--seed", type=int, default=0xC0FF2)
     ap.add_argument("--workload", choices=["partition", "quicksort", "batched", "serve"],
                     default="partition",
@@ -434,6 +436,8 @@ def run_ours(args):
     if clk:
         result["clocks"] = clk
 
+    if not args.no_yardstick and dt == "u64":
+        result["yardstick_cub"] = cub_yardstick(args, keys, n, pivot, stream, fill, seed0, t)
     if not args.no_e2e and dt == "u64":
         result["e2e"] = e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream)
     if rank == 0 and ws == 1 and not args.no_cpu and dt == "u64":
@@ -449,6 +453,53 @@ def run_ours(args):
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def cub_yardstick(args, keys, n, pivot, stream, fill, seed0, split_ours):
+    """The out-of-place library partition (CUB DevicePartition::If, built into
+    libyardstick.so) of the same input, timed the same way: what giving up the
+    in-place property buys at the same bandwidth.  Not the product path."""
+    import ctypes
+    import torch
+    path = os.path.join(ROOT, "paper_2004_12532_gb300", "libyardstick.so")
+    if not os.path.exists(path):
+        return {"unavailable": "libyardstick.so not built"}
+    L = ctypes.CDLL(path)
+    tb = ctypes.c_size_t()
+    if L.yd_cub_partition_temp_bytes(ctypes.c_uint64(n), ctypes.byref(tb)) != 0:
+        return {"unavailable": "temp size query failed"}
+    out = torch.empty_like(keys)
+    tmp = torch.empty(max(1, tb.value), dtype=torch.uint8, device="cuda")
+    sel = torch.zeros(1, dtype=torch.int64, device="cuda")
+    L.yd_cub_partition_u64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for k in range(max(3, args.warmup) + max(3, args.steps)):
+        fill(seed0 + k)
+        ev0.record(stream)
+        rc = L.yd_cub_partition_u64(keys.data_ptr(), out.data_ptr(), n, pivot, sel.data_ptr(),
+                                    tmp.data_ptr(), tb.value, stream.cuda_stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        if rc != 0:
+            return {"unavailable": "cub partition failed"}
+        if k >= max(3, args.warmup):
+            times.append(ev0.elapsed_time(ev1))
+    fill(seed0 + args.steps - 1)  # the last timed input of our partition, for the split
+    L.yd_cub_partition_u64(keys.data_ptr(), out.data_ptr(), n, pivot, sel.data_ptr(),
+                           tmp.data_ptr(), tb.value, stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = sum(times) / len(times)
+    res = {"kernel": "cub::DevicePartition::If (out of place)", "ms_per_step": ms,
+           "effective_gbs": 3 * 8 * n / (ms / 1e3) / 1e9,
+           "read_write_gbs": 2 * 8 * n / (ms / 1e3) / 1e9,
+           "extra_device_bytes": 8 * n + tb.value,
+           "same_split": int(sel.item()) == split_ours}
+    del out, tmp
+    return res
 
 
 def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):

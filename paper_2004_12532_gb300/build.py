@@ -16,6 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpartition.so")
+YARD = os.path.join(PKG, "yardstick")
+YLIB = os.path.join(PKG, "libyardstick.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -54,23 +56,33 @@ def _compile(src, extra):
     return obj
 
 
+def _link(target, objs, force):
+    if force or _stale(target, objs):
+        tmp = target + ".tmp%d" % os.getpid()
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        os.replace(tmp, target)
+
+
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    """Compile every source under csrc/ and link libpartition.so; return its path."""
+    """Compile every source under csrc/ and link libpartition.so, and the
+    out-of-place library yardstick (yardstick/) into libyardstick.so; return
+    the path of libpartition.so."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if force:
         for f in glob.glob(os.path.join(OUT_DIR, "*.o")):
             os.remove(f)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    ysrcs = sorted(glob.glob(os.path.join(YARD, "*.cu")))
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs) + len(ysrcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
+        yobjs = list(ex.map(lambda s: _compile(s, extra), ysrcs))
+    _link(LIB, objs, force)
+    if yobjs:
+        _link(YLIB, yobjs, force)
     return LIB
 
 
