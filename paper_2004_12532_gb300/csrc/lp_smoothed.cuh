@@ -137,6 +137,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
   const uint32_t lt = (1u << lane) - 1u;
   k = 0;
   if (nl <= 0) return true;
+  uint32_t kl = 0;  // this lane's predecessors (the group's k is their sum)
 
   // per-step constants in 32 bits
   const uint32_t g32 = (uint32_t)G.g, b32 = (uint32_t)G.b;
@@ -208,7 +209,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     }
     Lr.pred = pred;
     Lr.valid = valid;
-    k += __reduce_add_sync(FULL, __popc(pred));
+    kl += __popc(pred);
     __syncwarp();  // every lane has read the stage: it may be refilled
     if (pair_can_issue(c)) {
       if (st < kQ) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
@@ -355,7 +356,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
       as += __popc(bs);
     }
   }
-  __syncwarp();
+  k = __reduce_add_sync(FULL, kl);
   return true;
 }
 
