@@ -190,7 +190,7 @@ lp_status step_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t b, uint64_
   if (!vmin || !vmax || !count) return fail(c, LP_ERR_INVALID_ARG, "null result pointer");
   if (n > 0 && !keys) return fail(c, LP_ERR_INVALID_ARG, "null array");
   if (b == 0 || g == 0) return fail(c, LP_ERR_INVALID_ARG, "b and g must be positive");
-  if ((b * sizeof(T)) % 16 != 0 || b * sizeof(T) > lp::kLineBytesMax)
+  if ((b * sizeof(T)) % 16 != 0 || b * sizeof(T) > lp::max_line_bytes(sizeof(T)))
     return fail(c, LP_ERR_INVALID_ARG, "b*sizeof(key) must be a multiple of 16, at most 1024");
   if (!aligned_to(keys, 16) || (n * sizeof(T)) % 16 != 0)
     return fail(c, LP_ERR_MISALIGNED, "keys must be 16-byte aligned, n*sizeof(key) % 16 == 0");

@@ -9,6 +9,7 @@
 
 #include "lp_batched.h"
 #include "lp_ctx.h"
+#include "lp_plan.h"
 #include "lp_device.cuh"
 
 struct lp_batch {
@@ -84,8 +85,9 @@ extern "C" {
 
 lp_status lp_ctx_set_batch_tuning(lp_ctx* c, const lp_batch_tuning* t) {
   if (!c || !t) return LP_ERR_INVALID_ARG;
-  if (t->line_bytes && (t->line_bytes < 128 || t->line_bytes > 1024 || (t->line_bytes & 15)))
-    return lp_fail(c, LP_ERR_INVALID_ARG, "line_bytes must be a multiple of 16 in 128..1024");
+  if (t->line_bytes && (t->line_bytes < 128 || t->line_bytes > lp::kLineBytesMax ||
+                        (t->line_bytes & 15)))
+    return lp_fail(c, LP_ERR_INVALID_ARG, "line_bytes must be a multiple of 16 in 128..2048");
   c->tuning = *t;
   return LP_OK;
 }
@@ -260,7 +262,7 @@ lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t cou
   std::vector<lp_segment_u64> segs(count);
   for (uint32_t s = 0; s < count; s++) segs[s] = {d_keys + off[s], sizes[s], 0x7fffffffffffffffull};
   const lp_batch_tuning saved = c->tuning;
-  const uint32_t line_opts[] = {512, 1024};
+  const uint32_t line_opts[] = {1024, 2048};
   const uint32_t chunk_opts[] = {16, 32, 64, 128};
   const uint32_t cta_opts[] = {0, c->grid_batch_u64 / 2};
   cudaEvent_t e0, e1;

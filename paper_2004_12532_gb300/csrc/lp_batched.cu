@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   const uint32_t s_lo = (uint32_t)((uint64_t)count * blockIdx.x / gridDim.x);
   const uint32_t s_hi = (uint32_t)((uint64_t)count * (blockIdx.x + 1) / gridDim.x);
   if (lane == 0) {
-    for (uint32_t st = 0; st < kStages; st++) mbar_init(&ws.bar[st], 1);
+    for (uint32_t st = 0; st < R::Stages; st++) mbar_init(&ws.bar[st], 1);
     if (tid == 0) mbar_init(&cta_bar, 1);
     fence_mbar_init();
     fence_proxy_async_smem();
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
     }
     if (n_cta > 0) {  // CTA tasks first: they use the warps' shared memory
       if (lane == 0)
-        for (uint32_t st = 0; st < kStages; st++) mbar_inval(&ws.bar[st]);
+        for (uint32_t st = 0; st < R::Stages; st++) mbar_inval(&ws.bar[st]);
       __syncthreads();
       for (;;) {
         if (tid == 0) fetch = atomicAdd(&B.counters[1], 1u);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
         __syncthreads();
       }
       if (lane == 0) {
-        for (uint32_t st = 0; st < kStages; st++) mbar_init(&ws.bar[st], 1);
+        for (uint32_t st = 0; st < R::Stages; st++) mbar_init(&ws.bar[st], 1);
         fence_mbar_init();
         fence_proxy_async_smem();
       }
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   }
   __syncthreads();
   if (lane == 0) {
-    for (uint32_t st = 0; st < kStages; st++) mbar_inval(&ws.bar[st]);
+    for (uint32_t st = 0; st < R::Stages; st++) mbar_inval(&ws.bar[st]);
     if (tid == 0) mbar_inval(&cta_bar);
   }
 }
@@ -462,7 +462,8 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   if (tune.ctas && tune.ctas < grid) grid = tune.ctas;
   if (grid > kBatchMaxGrid) grid = kBatchMaxGrid;
   a.group_workers = tune.group_workers ? tune.group_workers : (uint64_t)grid * R::Warps;
-  a.line_bytes = tune.line_bytes ? tune.line_bytes : R::LineBytes;
+  a.line_bytes = tune.line_bytes && tune.line_bytes < R::LineBytes ? tune.line_bytes
+                                                                  : R::LineBytes;
   a.min_chunks = tune.min_chunks ? tune.min_chunks : 64;
   a.warp_cap = kWarpCapBytes / R::K;
   a.min_chunks_residual = tune.min_chunks_residual ? tune.min_chunks_residual : a.min_chunks;

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) partition_kernel(T* keys, 
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   WarpSmem<T, KV>& ws = reinterpret_cast<WarpSmem<T, KV>*>(smem_raw)[warp];
   if (lane == 0) {
-    for (uint32_t s = 0; s < kStages; s++) mbar_init(&ws.bar[s], 1);
+    for (uint32_t s = 0; s < Tr<T, KV>::Stages; s++) mbar_init(&ws.bar[s], 1);
     fence_mbar_init();
     fence_proxy_async_smem();
   }
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) partition_kernel(T* keys, 
 
     if (n <= coop_cap) {  // the paper's base case, on chip
       if (lane == 0)  // the finish reuses the stages' shared memory
-        for (uint32_t s2 = 0; s2 < kStages; s2++) mbar_inval(&ws.bar[s2]);
+        for (uint32_t s2 = 0; s2 < Tr<T, KV>::Stages; s2++) mbar_inval(&ws.bar[s2]);
       __syncthreads();
       const uint64_t t = coop_finish<T, KV>(base, vbase, n, pivot, S, smem_raw, &bar_flag);
       if (t == ~0ull) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint
   if (gw >= G.g) return;  // warps are independent: no CTA barrier below
   WarpSmem<T, KV>& ws = reinterpret_cast<WarpSmem<T, KV>*>(smem_raw)[warp];
   if (lane == 0) {
-    for (uint32_t s = 0; s < kStages; s++) mbar_init(&ws.bar[s], 1);
+    for (uint32_t s = 0; s < Tr<T, KV>::Stages; s++) mbar_init(&ws.bar[s], 1);
     fence_mbar_init();
     fence_proxy_async_smem();
   }

@@ -23,10 +23,13 @@ namespace lp {
 // partition of U_i", one processor per group).  A warp holds two lines of its
 // group in registers (the paper's `low` and `high` ends) and keeps kQ more
 // lines in flight per side in shared memory.
-constexpr uint32_t kLineBytesMax = 1024;   // largest line in key bytes (2 vectors per lane)
+constexpr uint32_t kLineBytesMax = 2048;   // largest line in key bytes (over all key types)
+// largest line of a key type: 2 KB for 8-byte keys (fewer, longer line pairs
+// per key), 1 KB for 4-byte keys (the registers of two lines)
+LP_HD constexpr uint32_t max_line_bytes(uint32_t key_bytes) {
+  return key_bytes == 8 ? 2048u : 1024u;
+}
 constexpr uint32_t kLineBytesMin = 128;    // smallest line used by the parameter rule
-constexpr uint32_t kQ = 4;                 // loads in flight per side (a power of two)
-constexpr uint32_t kStages = 2 * kQ;       // input stages per warp
 constexpr uint32_t kFinishBytes = 64 * 1024;  // ranges up to this size: one CTA in smem
 constexpr uint32_t kMinChunks = 8;         // lines per group, at least (when g > 1)
 
@@ -142,8 +145,9 @@ LP_HD StepParams choose_params(uint64_t n, uint32_t key_bytes, uint64_t workers,
 // whichever line became pure (L all predecessors, or R all successors; both
 // when the counts match), then takes the next line from that side.  When no
 // unread line is left, the line still in hand is partitioned on its own.
-// Lines are loaded ahead from both ends, kQ per side; `fi` / `bi` are the next
-// lines to load from the front / back, [fnext, bnext] the lines not yet taken.
+// Lines are loaded ahead from both ends, Q per side (Q a power of two; stages
+// 0..Q-1 hold front lines, Q..2Q-1 back lines); `fi` / `bi` are the next lines
+// to load from the front / back, [fnext, bnext] the lines not yet taken.
 struct PairCtl {
   int32_t nl;            // lines in the group
   int32_t fi, bi;        // next line to load from the front / the back
@@ -154,13 +158,16 @@ LP_HD void pair_init(PairCtl& c, int32_t nl) {
   c.nl = nl; c.fi = 0; c.bi = nl - 1; c.fnext = 0; c.bnext = nl - 1;
 }
 LP_HD bool pair_can_issue(const PairCtl& c) { return c.fi <= c.bi; }
-LP_HD uint32_t pair_stage_front(int32_t line) { return (uint32_t)line & (kQ - 1); }
+template <uint32_t Q>
+LP_HD uint32_t pair_stage_front(int32_t line) { return (uint32_t)line & (Q - 1); }
+template <uint32_t Q>
 LP_HD uint32_t pair_stage_back(const PairCtl& c, int32_t line) {
-  return kQ + ((uint32_t)(c.nl - 1 - line) & (kQ - 1));
+  return Q + ((uint32_t)(c.nl - 1 - line) & (Q - 1));
 }
 // Stage holding an issued line: lines below fi came from the front queue.
+template <uint32_t Q>
 LP_HD uint32_t pair_stage_of(const PairCtl& c, int32_t line) {
-  return line < c.fi ? pair_stage_front(line) : pair_stage_back(c, line);
+  return line < c.fi ? pair_stage_front<Q>(line) : pair_stage_back<Q>(c, line);
 }
 LP_HD bool pair_has_unread(const PairCtl& c) { return c.fnext <= c.bnext; }
 

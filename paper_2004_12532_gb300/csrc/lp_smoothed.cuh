@@ -16,7 +16,7 @@
 //   * whichever line became pure (L all predecessors, R all successors) is
 //     written straight back with coalesced 16-byte stores, and the next line
 //     of that side is taken; the last line left is partitioned on its own;
-//   * lane 0 keeps kQ lines per side in flight with 1-D bulk asynchronous
+//   * lane 0 keeps Q lines per side in flight with 1-D bulk asynchronous
 //     copies (TMA) into shared-memory stages, each completing on an mbarrier.
 // Every line is read once and written once: one read and one write of every
 // key, the I/O of the paper's Prop. 4.2.  The group ends predecessors first in
@@ -58,7 +58,10 @@ struct LevelArgs {
 template <typename T, bool KV>
 struct Tr {
   static constexpr uint32_t K = sizeof(T);
-  static constexpr uint32_t LineBytes = kLineBytesMax;          // key bytes per line, max
+  // key bytes per line, max; Q lines in flight per side
+  static constexpr uint32_t LineBytes = max_line_bytes(sizeof(T));
+  static constexpr uint32_t Q = LineBytes == 2048u ? 2u : 4u;
+  static constexpr uint32_t Stages = 2u * Q;
   static constexpr uint32_t LineKeys = LineBytes / K;
   static constexpr uint32_t V = 16u / K;                        // keys per 16-byte vector
   static constexpr uint32_t A = 16u / K;                        // alignment unit in keys
@@ -71,13 +74,14 @@ struct Tr {
 
 template <typename T, bool KV>
 struct __align__(128) WarpSmem {
-  T stage[kStages][Tr<T, KV>::LineKeys];
+  static constexpr uint32_t S = Tr<T, KV>::Stages;
+  T stage[S][Tr<T, KV>::LineKeys];
   T xbuf[2][Tr<T, KV>::LineKeys];
-  uint64_t vstage[KV ? kStages : 1][KV ? Tr<T, KV>::LineKeys : 2];
+  uint64_t vstage[KV ? S : 1][KV ? Tr<T, KV>::LineKeys : 2];
   uint64_t vxbuf[KV ? 2 : 1][KV ? Tr<T, KV>::LineKeys : 2];
-  uint64_t bar[kStages];
-  uint32_t st_line[kStages];   // line (within the range) loaded into each stage
-  uint32_t st_len[kStages];    // ... and its length in keys
+  uint64_t bar[S];
+  uint32_t st_line[S];   // line (within the range) loaded into each stage
+  uint32_t st_len[S];    // ... and its length in keys
 };
 
 template <typename T, bool KV>
@@ -185,7 +189,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
   };
   // take an issued line into registers; refill its stage; false on timeout
   auto take = [&](int32_t line, LineReg<T, KV>& Lr) -> bool {
-    const uint32_t st = pair_stage_of(c, line);
+    const uint32_t st = pair_stage_of<R::Q>(c, line);
     const bool arrived = mbar_wait_bounded(&sm.bar[st], (phase >> st) & 1u);
     if (!__all_sync(FULL, arrived)) return false;
     phase ^= 1u << st;
@@ -212,8 +216,8 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     kl += __popc(pred);
     __syncwarp();  // every lane has read the stage: it may be refilled
     if (pair_can_issue(c)) {
-      if (st < kQ) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
-      else { issue(c.bi, pair_stage_back(c, c.bi), false); c.bi--; }
+      if (st < R::Q) { issue(c.fi, pair_stage_front<R::Q>(c.fi), true); c.fi++; }
+      else { issue(c.bi, pair_stage_back<R::Q>(c, c.bi), false); c.bi--; }
     }
     return true;
   };
@@ -232,9 +236,9 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     }
   };
 
-  for (uint32_t q = 0; q < kQ; q++) {
-    if (pair_can_issue(c)) { issue(c.fi, pair_stage_front(c.fi), true); c.fi++; }
-    if (pair_can_issue(c)) { issue(c.bi, pair_stage_back(c, c.bi), false); c.bi--; }
+  for (uint32_t q = 0; q < R::Q; q++) {
+    if (pair_can_issue(c)) { issue(c.fi, pair_stage_front<R::Q>(c.fi), true); c.fi++; }
+    if (pair_can_issue(c)) { issue(c.bi, pair_stage_back<R::Q>(c, c.bi), false); c.bi--; }
   }
   __syncwarp();
 
@@ -318,7 +322,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
       atomicOr(status, kStatTimeout);
       for (int32_t l = c.fnext; l <= c.bnext; l++) {
         if (l >= c.fi && l <= c.bi) continue;  // never issued
-        const uint32_t s2 = pair_stage_of(c, l);
+        const uint32_t s2 = pair_stage_of<R::Q>(c, l);
         mbar_wait_bounded(&sm.bar[s2], (phase >> s2) & 1u);
       }
     }

@@ -35,7 +35,9 @@ static uint64_t rnd() {
     }                                         \
   } while (0)
 
+template <uint32_t Q>
 static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern) {
+  constexpr uint32_t kStages = 2 * Q;
   std::vector<std::vector<int64_t>> line(nl);
   int64_t id = 0;
   for (int64_t m = 0; m < nl; m++) {
@@ -87,8 +89,8 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern) {
     stage_uses[st]++;
   };
   auto take = [&](int64_t m, std::vector<int64_t>& reg) {
-    const uint32_t st = pair_stage_of(c, m);
-    const bool front_stage = st < kQ;
+    const uint32_t st = pair_stage_of<Q>(c, m);
+    const bool front_stage = st < Q;
     CHECK(stage_busy[st] && stage_line[st] == m, "stage %u does not hold line %lld", st,
           (long long)m);
     CHECK(((phase >> st) & 1u) == stage_parity[st], "parity mismatch");
@@ -100,11 +102,11 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern) {
     stage_busy[st] = 0;
     if (pair_can_issue(c)) {
       if (front_stage) {
-        CHECK(pair_stage_front(c.fi) == st, "front refill into another stage");
-        issue(c.fi, pair_stage_front(c.fi)); c.fi++;
+        CHECK(pair_stage_front<Q>(c.fi) == st, "front refill into another stage");
+        issue(c.fi, pair_stage_front<Q>(c.fi)); c.fi++;
       } else {
-        CHECK(pair_stage_back(c, c.bi) == st, "back refill into another stage");
-        issue(c.bi, pair_stage_back(c, c.bi)); c.bi--;
+        CHECK(pair_stage_back<Q>(c, c.bi) == st, "back refill into another stage");
+        issue(c.bi, pair_stage_back<Q>(c, c.bi)); c.bi--;
       }
     }
   };
@@ -115,9 +117,9 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern) {
     line[m] = reg;
   };
 
-  for (uint32_t q = 0; q < kQ; q++) {
-    if (pair_can_issue(c)) { issue(c.fi, pair_stage_front(c.fi)); c.fi++; }
-    if (pair_can_issue(c)) { issue(c.bi, pair_stage_back(c, c.bi)); c.bi--; }
+  for (uint32_t q = 0; q < Q; q++) {
+    if (pair_can_issue(c)) { issue(c.fi, pair_stage_front<Q>(c.fi)); c.fi++; }
+    if (pair_can_issue(c)) { issue(c.bi, pair_stage_back<Q>(c, c.bi)); c.bi--; }
   }
   std::vector<int64_t> L, R;
   int64_t lL = -1, lR = -1;
@@ -161,15 +163,17 @@ static void run_case(int64_t nl, uint64_t b, uint64_t last_len, int pattern) {
 int main(int argc, char** argv) {
   int cases = argc > 1 ? atoi(argv[1]) : 2000;
   rs ^= argc > 2 ? strtoull(argv[2], 0, 10) * 0x9E3779B97F4A7C15ull : 0;
-  // lines of the kernel: up to 1024 key bytes, whole 16-byte vectors
+  // lines of the kernel: up to 2048 key bytes, whole 16-byte vectors; both
+  // queue depths the kernels use (2 lines per side for 2 KB lines, 4 for 1 KB)
   for (int t = 0; t < cases; t++) {
     const uint32_t kpv = (rnd() & 1) ? 2 : 4;          // keys per vector (u64 / u32)
-    const uint32_t lv = 64u >> (rnd() % 4);             // vectors per line: 64..8
+    const uint32_t lv = 128u >> (rnd() % 5);            // vectors per line: 128..8
     const uint64_t b = (uint64_t)lv * kpv;
     const int64_t nl = 1 + (int64_t)(rnd() % (t % 3 == 0 ? 400 : 20));
     uint64_t last = b;
     if (rnd() % 2) last = kpv * (1 + rnd() % lv);
-    run_case(nl, b, last, (int)(rnd() % 9));
+    if (t & 1) run_case<2>(nl, b, last, (int)(rnd() % 9));
+    else run_case<4>(nl, b, last, (int)(rnd() % 9));
   }
   printf("OK\n");
   return 0;

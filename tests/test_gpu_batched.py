@@ -131,7 +131,7 @@ def test_batched_alone_equals_single(ctx):
 def test_autotune_and_tuned_run(ctx):
     sizes = inputs.log_uniform_sizes(64, 0x7E, 8, 20).tolist()
     best = lp.lp_autotune_batched_u64(ctx, sizes)
-    assert best["line_bytes"] in (512, 1024) and best["min_chunks"] > 0
+    assert best["line_bytes"] in (1024, 2048) and best["min_chunks"] > 0
     host, offs, pivots = make_batch(sizes, 12)
     buf = to_dev(host)
     views = [buf[o:o + n] for o, n in zip(offs, sizes)]

@@ -106,7 +106,7 @@ def test_step_rejects_bad_args(ctx):
         lp.lp_smoothed_step(ctx, dev, P50, 3, 4)  # 24-byte line
     assert e.value.status == lp.LP_ERR_INVALID_ARG
     with pytest.raises(lp.LPError) as e:
-        lp.lp_smoothed_step(ctx, dev, P50, 256, 4)  # 2048-byte line: above the limit
+        lp.lp_smoothed_step(ctx, dev, P50, 512, 4)  # 4096-byte line: above the limit
     assert e.value.status == lp.LP_ERR_INVALID_ARG
 
 
