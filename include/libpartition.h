@@ -99,7 +99,10 @@ lp_status lp_ctx_wait(lp_ctx *ctx);
  * ranges[4L..4L+3] = {lo, hi, b, g} of the range that level partitioned
  * (all zero for a level that had nothing left to do; g == 0 marks the on-chip
  * base case), and ms[L] = the level's duration in milliseconds from device
- * timestamps (ms may be NULL).  Synchronises the last call's stream.
+ * timestamps (ms may be NULL).  After an LP_LOWSPACE call (or
+ * lp_lowspace_partition_*) the entries are its phases instead: ms[0..4] =
+ * count, MakeSuccessorHeavy, block prefix, innermost prefix on chip, Reorder,
+ * with all ranges zero.  Synchronises the last call's stream.
  * *levels receives LP_MAX_LEVELS. */
 lp_status lp_ctx_level_stats(lp_ctx *ctx, uint64_t *ranges, float *ms, int *levels);
 /* Duration in milliseconds, from CUDA events on the call's stream, of the

@@ -104,6 +104,7 @@ lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot
   if (!c) return LP_ERR_INVALID_ARG;
   c->err.clear();
   c->last_launches = 0;
+  c->last_low_tl = nullptr;
   if (variant != LP_SMOOTHED && variant != LP_STRIDED && variant != LP_LOWSPACE &&
       variant != LP_HYBRID)
     return fail(c, LP_ERR_INVALID_ARG, "unknown variant");
@@ -135,6 +136,7 @@ lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot
   } else if (variant == LP_LOWSPACE) {
     lp_status ls = ensure_var(c, lp::lowspace_scratch_bytes(n, kLowspaceBlock, cfg.grid), stream);
     if (ls != LP_OK) return ls;
+    cfg.phase_stamps = &c->last_low_tl;
     e = cudaSuccess;
     // the status word and grid barrier start clean
     e = cudaMemsetAsync(S.status, 0, 4, stream);
@@ -240,6 +242,8 @@ lp_status lowspace_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t B, uin
   lp_status ls = ensure_var(c, lp::lowspace_scratch_bytes(n, B, cfg.grid), stream);
   if (ls != LP_OK) return ls;
   lp::TaskScratch S = c->task;
+  c->last_low_tl = nullptr;
+  cfg.phase_stamps = &c->last_low_tl;
   e = cudaMemsetAsync(S.status, 0, 4, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.bar, 0, 8, stream);
   if (e == cudaSuccess)
@@ -331,6 +335,20 @@ lp_status lp_ctx_level_stats(lp_ctx* c, uint64_t* ranges, float* ms, int* levels
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   e = cudaStreamSynchronize(c->last_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  if (c->last_low_tl) {  // a low-space call: its phases in place of levels
+    unsigned long long t[lp::kLowPhases];
+    e = cudaMemcpy(t, c->last_low_tl, sizeof(t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read phases");
+    for (int L = 0; L < lp::kMaxLevels; L++) {
+      for (int q = 0; q < 4; q++) ranges[4 * L + q] = 0;
+      if (ms) {
+        const bool have = L + 1 < lp::kLowPhases && t[L] && t[L + 1] >= t[L];
+        ms[L] = have ? (float)((double)(t[L + 1] - t[L]) * 1e-6) : 0.f;
+      }
+    }
+    *levels = lp::kMaxLevels;
+    return LP_OK;
+  }
   const size_t db = lp::level_desc_bytes();
   uint64_t w[lp::kMaxLevels][8];
   e = cudaMemcpy(w, c->task.desc, db * lp::kMaxLevels, cudaMemcpyDeviceToHost);

@@ -37,6 +37,7 @@ struct lp_ctx {
   unsigned long long* last_batch_traffic = nullptr;  // streamed-keys counter of the last batch
   unsigned long long* last_batch_tround = nullptr;   // its round timestamps
   lp_sort_stats sort_stats{};                         // of the last quicksort
+  unsigned long long* last_low_tl = nullptr;          // phase stamps of the last LP_LOWSPACE call
 };
 
 

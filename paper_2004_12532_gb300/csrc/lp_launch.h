@@ -30,7 +30,13 @@ struct LaunchCfg {
   cudaStream_t stream;
   uint64_t launches;   // incremented per kernel launch
   cudaEvent_t* events; // optional: two events around the partition kernel
+  unsigned long long** phase_stamps = nullptr;  // optional: receives the low-space
+                                                // kernel's phase timestamps (device)
 };
+
+// phases of the low-space kernel with a timestamp each: start, count,
+// MakeSuccessorHeavy, block prefix, innermost prefix on chip, Reorder
+constexpr int kLowPhases = 6;
 
 // Keys-only (KV = false, vals == nullptr) and key+payload (KV = true, T = uint64_t).
 // Full Recursive Smoothed Striding partition (strided != 0: the first step uses

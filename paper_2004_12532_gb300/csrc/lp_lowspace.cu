@@ -18,7 +18,8 @@
 //      on chip; then, from the inside out, every predecessor of a block beyond
 //      P_{j+1} is swapped with position v[i-1] + (its rank in the block), a
 //      successor inside P_{j+1} -- conflict-free because P_{j+1} is
-//      successor-heavy.
+//      successor-heavy; one warp per block, its rounds of 32 keys ranked by
+//      ballots.
 // Every load of keys that another CTA may have written goes through L2
 // (ld.global.cg), so no CTA reads a stale L1 line after a barrier.
 #include <cuda_runtime.h>
@@ -33,6 +34,7 @@ namespace {
 
 constexpr uint32_t kLT = 256;               // threads per CTA
 constexpr uint64_t kMshSmall = 1u << 15;    // pair counts below this: one CTA
+constexpr uint32_t kUnroll = 8;             // independent loads in flight per thread
 constexpr int kMaxReorderLevels = 96;
 
 struct LowArgs {
@@ -46,6 +48,7 @@ struct LowArgs {
   unsigned long long* cta;         // one word per CTA
   unsigned long long* total;       // predecessor count of the range
   uint64_t* split;                 // if set: the split (count) is written here
+  unsigned long long* tl;          // device timestamps: start, then the end of each phase
 };
 
 template <typename T>
@@ -69,12 +72,11 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long x,
 }
 
 template <typename T, bool KV>
-__global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, LowArgs a,
+__global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* vals, LowArgs a,
                                                        TaskScratch S) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ unsigned int flag;
   __shared__ unsigned long long red[kLT / 32];
-  __shared__ uint32_t wc[16][kLT / 32];
   __shared__ uint64_t levM[kMaxReorderLevels], levT[kMaxReorderLevels], levNB[kMaxReorderLevels];
   __shared__ int nlev;
   __shared__ uint64_t mbase_s;
@@ -95,17 +97,32 @@ __global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, 
   T* A = keys + lo;
   uint64_t* Y = KV ? vals + lo : nullptr;
   const T pivot = (T)a.pivot;
+  auto stamp = [&](int k) {
+    if (leader) a.tl[k] = global_timer_ns();
+  };
+  stamp(0);
 
   // ---- 1. count, role swap
   {
     unsigned long long c = 0;
-    for (uint64_t q = gtid; q < n; q += gstride) c += ldcg(&A[q]) <= pivot;
+    for (uint64_t q0 = gtid; q0 < n; q0 += kUnroll * gstride) {  // kUnroll loads in flight
+      T x[kUnroll];
+#pragma unroll
+      for (uint32_t u = 0; u < kUnroll; u++) {
+        const uint64_t q = q0 + u * gstride;
+        x[u] = q < n ? ldcg(&A[q]) : pivot;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kUnroll; u++)
+        c += (q0 + u * gstride < n && x[u] <= pivot) ? 1u : 0u;
+    }
     c = cta_sum(c, red);
     if (tid == 0) atomicAdd(a.total, c);
   }
   if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   const uint64_t cnt = __ldcg(a.total);
   if (leader && a.split) *a.split = cnt;
+  stamp(1);
   if (n < 2) return;
   const bool flip = 2 * (n - cnt) < n;
   auto mem = [&](uint64_t i) -> uint64_t { return flip ? n - 1 - i : i; };
@@ -125,20 +142,17 @@ __global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, 
   while (m > 1) {
     const uint64_t half = m / 2;
     if (half >= kMshSmall) {
-      for (uint64_t i0 = gtid; i0 < half; i0 += 4 * gstride) {
-        T x[4], y[4];
-        uint64_t p[4], q[4];
+      for (uint64_t i0 = gtid; i0 < half; i0 += kUnroll * gstride) {
+        T x[kUnroll], y[kUnroll];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (uint32_t u = 0; u < kUnroll; u++) {
           const uint64_t i = i0 + u * gstride;
-          p[u] = mem(i);
-          q[u] = mem(m - 1 - i);
-          if (i < half) { x[u] = ldcg(&A[p[u]]); y[u] = ldcg(&A[q[u]]); }
+          if (i < half) { x[u] = ldcg(&A[mem(i)]); y[u] = ldcg(&A[mem(m - 1 - i)]); }
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (uint32_t u = 0; u < kUnroll; u++) {
           const uint64_t i = i0 + u * gstride;
-          if (i < half && isp(x[u]) && !isp(y[u])) swap_at(p[u], q[u], x[u], y[u]);
+          if (i < half && isp(x[u]) && !isp(y[u])) swap_at(mem(i), mem(m - 1 - i), x[u], y[u]);
         }
       }
       if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
@@ -161,6 +175,8 @@ __global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, 
     }
   }
 
+  stamp(2);
+
   // ---- 3. block prefix v[i]
   const uint64_t B = a.B;
   const uint64_t nb = n / B;
@@ -175,7 +191,17 @@ __global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, 
     for (uint64_t b = b0; b < b1; b++) {
       const uint64_t s = b * B, e = (b + 1 == nb) ? n : s + B;
       unsigned long long c = 0;
-      for (uint64_t q = s + tid; q < e; q += kLT) c += isp(ldcg(&A[mem(q)]));
+      for (uint64_t q0 = s + tid; q0 < e; q0 += (uint64_t)kUnroll * kLT) {
+        T x[kUnroll];
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; u++) {
+          const uint64_t q = q0 + (uint64_t)u * kLT;
+          if (q < e) x[u] = ldcg(&A[mem(q)]);
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; u++)
+          c += (q0 + (uint64_t)u * kLT < e && isp(x[u])) ? 1u : 0u;
+      }
       c = cta_sum(c, red);
       run += c;
       if (tid == 0) __stcg(reinterpret_cast<unsigned long long*>(&a.v[b]), run);
@@ -191,6 +217,8 @@ __global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, 
     }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }
+
+  stamp(3);
 
   // ---- 4. Reorder: the prefix levels, innermost first
   if (tid == 0) {
@@ -221,66 +249,57 @@ __global__ void __launch_bounds__(kLT) lowspace_kernel(T* keys, uint64_t* vals, 
     if (t == ~0ull) { fail(); return; }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }
+  stamp(4);
+  // Reorder level by level, outward; one warp per block, kUnroll rounds of 32
+  // keys in flight: every predecessor of block i goes to v[i-1] + its rank in
+  // the block (a successor inside the successor-heavy prefix), so the target
+  // loads of a group of rounds can all be issued before its stores
+  const uint64_t gwarp = ((uint64_t)blockIdx.x * kLT + tid) >> 5;
+  const uint64_t nwarps = gstride >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
   for (int j = L - 1; j >= 0; j--) {
     const uint64_t M = levM[j], t0 = levT[j], NB = levNB[j];
-    for (uint64_t i = t0 + blockIdx.x; i < NB; i += gridDim.x) {
-      const uint64_t s = i * B, e = (i + 1 == NB) ? M : s + B;
+    for (uint64_t i = t0 + gwarp; i < NB; i += nwarps) {
+      const uint64_t s0 = i * B, e = (i + 1 == NB) ? M : s0 + B;
       uint64_t y = __ldcg(reinterpret_cast<const unsigned long long*>(&a.v[i - 1]));
-      // the block, in rounds of kLT keys; up to 16 rounds of ranks per pass
-      for (uint64_t r0 = s; r0 < e; r0 += 16ull * kLT) {
-        T x[16];
-        uint32_t f = 0;
-        const uint64_t rr_ = (e - r0 + kLT - 1) / kLT;
-        const uint32_t rounds = (uint32_t)(rr_ < 16 ? rr_ : 16);
+      for (uint64_t r0 = s0; r0 < e; r0 += 32ull * kUnroll) {
+        T x[kUnroll], z[kUnroll];
+        uint64_t tg[kUnroll];
+        uint32_t f = 0, bal[kUnroll];
 #pragma unroll
-        for (uint32_t k = 0; k < 16; k++) {
-          const uint64_t q = r0 + (uint64_t)k * kLT + tid;
-          if (k < rounds && q < e) {
-            x[k] = ldcg(&A[mem(q)]);
-            f |= (isp(x[k]) ? 1u : 0u) << k;
+        for (uint32_t u = 0; u < kUnroll; u++) {
+          const uint64_t q = r0 + 32ull * u + lane;
+          if (q < e) {
+            x[u] = ldcg(&A[mem(q)]);
+            f |= (isp(x[u]) ? 1u : 0u) << u;
           }
         }
-        uint32_t bal[16];
+        uint32_t run = 0;
 #pragma unroll
-        for (uint32_t k = 0; k < 16; k++) {
-          bal[k] = __ballot_sync(0xffffffffu, (f >> k) & 1u);
-          if (lane == 0 && k < rounds) wc[k][warp] = __popc(bal[k]);
-        }
-        __syncthreads();
-        // exclusive offsets in (round, warp) order
-        uint64_t base = y;
-        uint32_t total = 0;
-        for (uint32_t k = 0; k < rounds; k++)
-          for (uint32_t w = 0; w < kLT / 32; w++) total += wc[k][w];
-#pragma unroll
-        for (uint32_t k = 0; k < 16; k++) {
-          if (k >= rounds) break;
-          uint32_t before = 0;
-          for (uint32_t w = 0; w < warp; w++) before += wc[k][w];
-          if ((f >> k) & 1u) {
-            const uint64_t T_ = base + before + __popc(bal[k] & ((1u << lane) - 1u));
-            const uint64_t tm = mem(T_);
-            const uint64_t pm = mem(r0 + (uint64_t)k * kLT + tid);
-            const T z = ldcg(&A[tm]);
-            swap_at(tm, pm, z, x[k]);  // A[tm] <- x[k], A[pm] <- z
+        for (uint32_t u = 0; u < kUnroll; u++) {
+          bal[u] = __ballot_sync(0xffffffffu, (f >> u) & 1u);
+          if ((f >> u) & 1u) {
+            tg[u] = mem(y + run + __popc(bal[u] & lt));
+            z[u] = ldcg(&A[tg[u]]);
           }
-          uint32_t tk = 0;
-          for (uint32_t w = 0; w < kLT / 32; w++) tk += wc[k][w];
-          base += tk;
+          run += __popc(bal[u]);
         }
-        y += total;
-        __syncthreads();  // wc reuse
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; u++)
+          if ((f >> u) & 1u) swap_at(tg[u], mem(r0 + 32ull * u + lane), z[u], x[u]);
+        y += run;
       }
     }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }
+  stamp(5);
 }
 
 }  // namespace
 
 size_t lowspace_scratch_bytes(uint64_t n, uint64_t B, uint32_t grid) {
   const uint64_t nb = B ? n / B : 0;
-  return ((nb + 1) * 8 + 255) / 256 * 256 + ((size_t)grid * 8 + 255) / 256 * 256 + 256;
+  return ((nb + 1) * 8 + 255) / 256 * 256 + ((size_t)grid * 8 + 255) / 256 * 256 + 256 + 256;
 }
 
 template <typename T, bool KV>
@@ -304,6 +323,7 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
   a.cta = reinterpret_cast<unsigned long long*>(p);
   p += ((size_t)cfg.grid * 8 + 255) / 256 * 256;
   a.total = reinterpret_cast<unsigned long long*>(p);
+  a.tl = reinterpret_cast<unsigned long long*>(p + 256);
   a.split = split;
   const size_t smem = level_smem_bytes<T, KV>();
   cudaError_t e = cudaFuncSetAttribute(lowspace_kernel<T, KV>,
@@ -323,7 +343,9 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
   a.base_keys = base_keys < cap ? base_keys : cap;
   if (a.base_keys < 5 * B) a.base_keys = 0;  // the paper's base case decides
   e = cudaMemsetAsync(a.total, 0, 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.tl, 0, 8 * kLowPhases, st);
   if (e != cudaSuccess) return e;
+  if (cfg.phase_stamps) *cfg.phase_stamps = a.tl;
   e = launch_cooperative(lowspace_kernel<T, KV>, grid, kLT, smem, st, keys, vals, a, S);
   cfg.launches++;
   return e;
