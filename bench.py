@@ -397,14 +397,22 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     k_ms = sum(kern_ms) / len(kern_ms)
     k_keys = sum(traffic_keys) / len(traffic_keys)
-    k_bytes = 2 * E * k_keys  # one read and one write of every key of every level
+    kname = {"u64": "uint64_t", "u32": "uint32_t", "kv": "uint64_t, payload"}[dt]
+    if args.variant == "lowspace":
+        # Sec. 5's accounting of the low-space partition: 3.5 read/write passes
+        # and 0.5 read pass over the keys, i.e. 7.5 key bytes per key
+        k_bytes = 7.5 * E * n
+        kernel = "lowspace_kernel<%s> (all phases, one cooperative launch)" % kname
+        traffic = None
+    else:
+        k_bytes = 2 * E * k_keys  # one read and one write of every key of every level
+        kernel = "partition_kernel<%s> (all levels, one cooperative launch)" % kname
+        traffic = profiled_traffic(k_keys) if dt == "u64" and args.variant == "smoothed" \
+            else None
     achieved = k_bytes / (k_ms / 1e3) / 1e9
-    traffic = profiled_traffic(k_keys) if dt == "u64" else None
     l0_ms = sum(lvl0_ms) / len(lvl0_ms)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "partition_kernel<%s> (all levels, one cooperative launch)" % (
-                    {"u64": "uint64_t", "u32": "uint32_t", "kv": "uint64_t, payload"}[dt]),
+                "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": k_bytes,
                 "ms_per_launch": k_ms,
                 "level0_gbs_device_timestamps": 2 * E * (sum(lvl0_n) / len(lvl0_n)) /
