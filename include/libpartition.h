@@ -158,8 +158,7 @@ typedef struct {
  * them. */
 typedef struct {
   uint32_t ctas;          /* CTAs of the persistent launch (<= lp_ctx_grid) */
-  uint32_t line_bytes;    /* line size b * key bytes of the steps: 128 .. 2048
-                             (at most 1024 for uint32 keys) */
+  uint32_t line_bytes;    /* line size b * key bytes of the steps: 128 .. 2048 */
   uint32_t min_chunks;    /* lines per group, at least */
   uint32_t group_workers; /* groups per segment step, at most */
   uint32_t min_chunks_residual; /* lines per group, at least, in steps after the first */
@@ -379,7 +378,7 @@ lp_status lp_lowspace_partition_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uin
  * has none); *count = number of predecessors.  Afterwards keys[p] <= pivot
  * for p < vmin and keys[p] > pivot for p >= vmax.
  * Requires keys 16-byte aligned, n * sizeof(key) and b * sizeof(key)
- * multiples of 16, b * sizeof(key) <= 2048 (uint64) or 1024 (uint32), g >= 1; otherwise
+ * multiples of 16, b * sizeof(key) <= 2048, g >= 1; otherwise
  * LP_ERR_MISALIGNED / LP_ERR_INVALID_ARG.  Synchronises `stream`. */
 lp_status lp_smoothed_step_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
                                uint64_t b, uint64_t g, uint64_t seed, uint64_t level,

@@ -83,7 +83,7 @@ struct PartArgs {
 
 // The whole recursion in one cooperative launch; see the file comment.
 template <typename T, bool KV>
-__global__ void __launch_bounds__(Tr<T, KV>::Threads) partition_kernel(T* keys, uint64_t* vals,
+__global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* keys, uint64_t* vals,
                                                                        PartArgs a,
                                                                        TaskScratch S) {
   using R = Tr<T, KV>;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads) partition_kernel(T* keys, 
 
 // One Partial Partition Step with explicit parameters on [a.lo, a.hi).
 template <typename T, bool KV>
-__global__ void __launch_bounds__(Tr<T, KV>::Threads) level_kernel(T* keys, uint64_t* vals,
+__global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) level_kernel(T* keys, uint64_t* vals,
                                                                    LevelArgs a, LevelDesc* out,
                                                                    uint32_t* status) {
   using R = Tr<T, KV>;

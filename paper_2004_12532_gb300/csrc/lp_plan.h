@@ -24,10 +24,10 @@ namespace lp {
 // group in registers (the paper's `low` and `high` ends) and keeps kQ more
 // lines in flight per side in shared memory.
 constexpr uint32_t kLineBytesMax = 2048;   // largest line in key bytes (over all key types)
-// largest line of a key type: 2 KB for 8-byte keys (fewer, longer line pairs
-// per key), 1 KB for 4-byte keys (the registers of two lines)
+// largest line of a key type: 2 KB (fewer, longer line pairs per key; the
+// kernels cap their registers so that two CTAs share an SM)
 LP_HD constexpr uint32_t max_line_bytes(uint32_t key_bytes) {
-  return key_bytes == 8 ? 2048u : 1024u;
+  return key_bytes == 8 || key_bytes == 4 ? 2048u : 1024u;
 }
 constexpr uint32_t kLineBytesMin = 128;    // smallest line used by the parameter rule
 constexpr uint32_t kFinishBytes = 64 * 1024;  // ranges up to this size: one CTA in smem
