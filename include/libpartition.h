@@ -346,6 +346,15 @@ lp_status lp_server_streamed_keys(lp_server *server, uint64_t *keys_u64, uint64_
 lp_status lp_server_run(lp_server *server, const lp_request *reqs, uint32_t count,
                         uint32_t mode, lp_completion *out);
 
+/* ------------------------------------------------------------ diagnostics
+ * Runs one kernel that waits on an mbarrier phase nothing completes and on a
+ * grid barrier for two CTAs in a grid of one: both waits must give up after
+ * the library's limit (about one second each) -- the mechanism behind
+ * LP_ERR_TIMEOUT -- and the device stays usable.  *mbar_gave_up and
+ * *grid_gave_up receive 1 when the respective wait gave up.  Takes about two
+ * seconds; synchronises the device. */
+lp_status lp_selftest_bounded_waits(int device, uint32_t *mbar_gave_up, uint32_t *grid_gave_up);
+
 /* ------------------------------------------ Blocked-Prefix-Sum partition
  * The low-space partition of Sec. 3 with explicit block size: count the
  * predecessors (swapping the roles on the reversed array when they are the

@@ -138,6 +138,7 @@ _SIGS = {
     "lp_server_get_stats": (_i, [_p, _p]),
     "lp_server_streamed_keys": (_i, [_p, _pu64, _pu64]),
     "lp_server_run": (_i, [_p, _p, _u32, _u32, _p]),
+    "lp_selftest_bounded_waits": (_i, [_i, C.POINTER(_u32), C.POINTER(_u32)]),
     "lp_fill_uniform_u64": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_uniform_u32": (_i, [_p, _u64, _u64, _p]),
     "lp_fill_iota_u64": (_i, [_p, _u64, _p]),
@@ -574,3 +575,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def lp_selftest_bounded_waits(device=0):
+    """(mbarrier wait gave up, grid barrier gave up): both 1 on a working build."""
+    a, b = C.c_uint32(), C.c_uint32()
+    st = lib().lp_selftest_bounded_waits(int(device), C.byref(a), C.byref(b))
+    if st != LP_OK:
+        raise LPError(st, "lp_selftest_bounded_waits")
+    return int(a.value), int(b.value)
