@@ -188,6 +188,35 @@ def cpu_oracle_gbs(log2n_sample, pivot, seed, min_seconds=8.0, max_reps=5):
     return 3 * 8 * n / med / 1e9, n, len(times), med
 
 
+def cpu_parallel_gbs(log2n, pivot, seed, reps=3):
+    """The Smoothed Striding partition on all host cores (OpenMP, libcpuyard.so):
+    the paper's own multicore setting, as a second CPU baseline."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2004_12532_gb300", "libcpuyard.so")
+    if not os.path.exists(path):
+        return {"unavailable": "libcpuyard.so not built"}
+    L = ctypes.CDLL(path)
+    L.cy_smoothed_partition_u64.restype = ctypes.c_uint64
+    L.cy_smoothed_partition_u64.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_int, ctypes.c_uint64]
+    n = 1 << log2n
+    threads = os.cpu_count() or 1
+    times, ok = [], True
+    for r in range(reps):
+        a = inputs.uniform_u64(n, seed + r)
+        want = int(np.count_nonzero(a <= np.uint64(pivot)))
+        t0 = time.perf_counter()
+        t = L.cy_smoothed_partition_u64(a.ctypes.data, n, pivot, threads, seed + r)
+        times.append(time.perf_counter() - t0)
+        ok = ok and t == want and bool(np.all(a[:t] <= np.uint64(pivot))) and \
+            bool(np.all(a[t:] > np.uint64(pivot)))
+    med = statistics.median(times)
+    return {"value": 3 * 8 * n / med / 1e9, "unit": "GB/s", "cores": threads,
+            "kind": "Smoothed Striding on the host cores (OpenMP)",
+            "sample": "2^%d uint64 keys, same distribution and pivot, median of %d runs" % (
+                log2n, reps), "correct": ok}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -449,6 +478,7 @@ def run_ours(args):
     if not args.no_e2e and dt == "u64":
         result["e2e"] = e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream)
     if rank == 0 and ws == 1 and not args.no_cpu and dt == "u64":
+        result["cpu_parallel"] = cpu_parallel_gbs(min(args.log2n, 27), pivot, args.seed)
         gbs, ns, reps, med = cpu_oracle_gbs(min(args.log2n, 27), pivot, args.seed)
         result["cpu_baseline"] = {
             "value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",

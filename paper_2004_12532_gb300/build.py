@@ -18,6 +18,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpartition.so")
 YARD = os.path.join(PKG, "yardstick")
 YLIB = os.path.join(PKG, "libyardstick.so")
+CLIB = os.path.join(PKG, "libcpuyard.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -83,7 +84,24 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     _link(LIB, objs, force)
     if yobjs:
         _link(YLIB, yobjs, force)
+    _build_cpu_yardstick(force)
     return LIB
+
+
+def _build_cpu_yardstick(force):
+    """The host-core Smoothed Striding yardstick (yardstick/*.c, OpenMP)."""
+    srcs = sorted(glob.glob(os.path.join(YARD, "*.c")))
+    if not srcs or not (force or _stale(CLIB, srcs + [__file__])):
+        return
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        return  # optional: the bench reports it as unavailable
+    tmp = CLIB + ".tmp%d" % os.getpid()
+    r = subprocess.run([cc, "-O3", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + srcs,
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("cpu yardstick build failed:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, CLIB)
 
 
 if __name__ == "__main__":
