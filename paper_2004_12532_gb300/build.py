@@ -99,8 +99,9 @@ def _build_cpu_yardstick(force):
     tmp = CLIB + ".tmp%d" % os.getpid()
     r = subprocess.run([cc, "-O3", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + srcs,
                        capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("cpu yardstick build failed:\n%s\n%s" % (r.stdout, r.stderr))
+    if r.returncode != 0:  # optional: the bench reports it as unavailable
+        sys.stderr.write("note: host-core yardstick not built:\n%s\n" % r.stderr[-2000:])
+        return
     os.replace(tmp, CLIB)
 
 
