@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--input", choices=["uniform", "sorted", "reverse", "dup16"],
                     default="uniform", help="quicksort input")
     ap.add_argument("--instances", type=int, default=4096, help="batched: instance count")
+    ap.add_argument("--min-chunks", type=int, default=0,
+                    help="quicksort: lines per group, at least, of the batched steps (0: default)")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests per step")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per s")
     ap.add_argument("--budget-gib", type=float, default=64.0, help="serve: HBM budget")
@@ -644,6 +646,8 @@ def run_quicksort(args):
     keys = torch.empty(n, dtype=torch.int64, device="cuda")
     ctx = lp.Ctx(local)
     ctx.set_timing(True)
+    if args.min_chunks:
+        lp.lp_ctx_set_batch_tuning(ctx, min_chunks=args.min_chunks)
     stream = torch.cuda.current_stream()
     seed0 = args.seed + 7919 * rank
     for w in range(args.warmup):

@@ -464,7 +464,7 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   a.group_workers = tune.group_workers ? tune.group_workers : (uint64_t)grid * R::Warps;
   a.line_bytes = tune.line_bytes && tune.line_bytes < R::LineBytes ? tune.line_bytes
                                                                   : R::LineBytes;
-  a.min_chunks = tune.min_chunks ? tune.min_chunks : 64;
+  a.min_chunks = tune.min_chunks ? tune.min_chunks : 32;
   a.warp_cap = kWarpCapBytes / R::K;
   a.min_chunks_residual = tune.min_chunks_residual ? tune.min_chunks_residual : a.min_chunks;
   const size_t smem = level_smem_bytes<T, false>();  // attribute set by batched_prepare
