@@ -9,9 +9,12 @@
 //      work on the logically reversed array (ParallelPartition's role swap);
 //   2. MakeSuccessorHeavy (Lemma 3.1): for i < floor(m/2) swap A[i] and
 //      A[m-1-i] when the first is a predecessor and the second a successor,
-//      then m <- ceil(m/2); small levels run inside one CTA;
+//      then m <- ceil(m/2); four levels per pass (three with payloads), each
+//      thread holding one component of positions in registers, and the
+//      passes below 2^16 keys inside one CTA;
 //   3. block counts and their prefix: v[i] = predecessors in blocks 0..i
-//      (blocks of B keys, the last block takes the remainder);
+//      (blocks of B keys, the last block takes the remainder), one warp per
+//      block, then a scan inside each CTA and across the CTAs;
 //   4. Reorder (Lemma "Reordering phase"): the prefixes P_0 ⊃ P_1 ⊃ ... with
 //      P_{j+1} the smallest prefix of whole blocks holding 4/5 of P_j; the
 //      innermost prefix (at most base_keys, or the paper's 5B) is partitioned
@@ -19,7 +22,7 @@
 //      P_{j+1} is swapped with position v[i-1] + (its rank in the block), a
 //      successor inside P_{j+1} -- conflict-free because P_{j+1} is
 //      successor-heavy; one warp per block, its rounds of 32 keys ranked by
-//      ballots.
+//      ballots, the next round's keys loading while a round's targets do.
 // Every load of keys that another CTA may have written goes through L2
 // (ld.global.cg), so no CTA reads a stale L1 line after a barrier.
 #include <cuda_runtime.h>
@@ -35,6 +38,7 @@ namespace {
 constexpr uint32_t kLT = 256;               // threads per CTA
 constexpr uint64_t kMshSmall = 1u << 15;    // pair counts below this: one CTA
 constexpr uint32_t kUnroll = 8;             // independent loads in flight per thread
+constexpr uint32_t kUnroll2 = 16;           // the same, where a lane has nothing else to hold
 constexpr int kMaxReorderLevels = 96;
 
 struct LowArgs {
@@ -69,6 +73,101 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long x,
   unsigned long long s = 0;
   for (uint32_t w = 0; w < kLT / 32; w++) s += red[w];
   return s;
+}
+
+// MakeSuccessorHeavy level k works on the prefix of m_k keys: it pairs i with
+// m_k - 1 - i for i < h_k = floor(m_k / 2), and m_{k+1} = m_k - h_k.  Over L
+// consecutive levels the positions fall into independent components: a root
+// r < m_L, its level-(L-1) partner, their level-(L-2) partners, and so on, at
+// most 2^L positions.  A pass loads one component into registers, applies the
+// L levels' swaps in order and stores the positions that changed, so each
+// position is read and written once per L levels instead of once per level.
+template <bool KV>
+constexpr int kMshFuse = KV ? 3 : 4;
+
+template <int L>
+__device__ __forceinline__ uint64_t msh_after(uint64_t m) {
+#pragma unroll
+  for (int k = 0; k < L; k++) m -= m / 2;
+  return m;
+}
+
+// Components rooted at r = r0, r0 + rstride, ... < m_L, all in flight at
+// once: slot j + 2^t holds the level-(L-1-t) partner of slot j (when it
+// exists), so level k pairs slot j with slot j + 2^(L-1-k).
+template <int L, typename T, bool KV, typename Mem, typename Isp>
+__device__ __forceinline__ void msh_pass(T* A, uint64_t* Y, uint64_t m, uint64_t r0,
+                                         uint64_t rstride, const Mem& mem, const Isp& isp) {
+  constexpr int W = 1 << L;
+  uint64_t mk[L], hk[L];
+  uint64_t mm = m;
+#pragma unroll
+  for (int k = 0; k < L; k++) {
+    mk[k] = mm;
+    hk[k] = mm / 2;
+    mm -= hk[k];
+  }
+  const uint64_t roots = mm;
+  for (uint64_t r = r0; r < roots; r += rstride) {
+    uint64_t x[W];
+    uint32_t valid = 1;
+    x[0] = r;
+#pragma unroll
+    for (int t = 0; t < L; t++) {
+      const int k = L - 1 - t;
+#pragma unroll
+      for (int j = 0; j < (1 << t); j++) {
+        const bool v = ((valid >> j) & 1u) && x[j] < hk[k];
+        x[j + (1 << t)] = mk[k] - 1 - x[j];
+        valid |= (uint32_t)v << (j + (1 << t));
+      }
+    }
+    T key[W];
+    uint64_t pos[W];
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      pos[j] = mem(x[j]);
+      if ((valid >> j) & 1u) key[j] = ldcg(&A[pos[j]]);
+    }
+    uint64_t src[KV ? W : 1];
+    if constexpr (KV) {
+#pragma unroll
+      for (int j = 0; j < W; j++) src[j] = pos[j];
+    }
+    uint32_t changed = 0;
+#pragma unroll
+    for (int k = 0; k < L; k++) {
+      const int t = L - 1 - k;
+#pragma unroll
+      for (int j = 0; j < (1 << t); j++) {
+        const int q = j + (1 << t);
+        if (((valid >> q) & 1u) && isp(key[j]) && !isp(key[q])) {
+          const T u = key[j];
+          key[j] = key[q];
+          key[q] = u;
+          changed |= (1u << j) | (1u << q);
+          if constexpr (KV) {
+            const uint64_t w = src[j];
+            src[j] = src[q];
+            src[q] = w;
+          }
+        }
+      }
+    }
+    if (!changed) continue;
+    if constexpr (KV) {
+      uint64_t yv[W];
+#pragma unroll
+      for (int j = 0; j < W; j++)
+        if ((changed >> j) & 1u) yv[j] = ldcg(&Y[src[j]]);
+#pragma unroll
+      for (int j = 0; j < W; j++)
+        if ((changed >> j) & 1u) Y[pos[j]] = yv[j];
+    }
+#pragma unroll
+    for (int j = 0; j < W; j++)
+      if ((changed >> j) & 1u) A[pos[j]] = key[j];
+  }
 }
 
 template <typename T, bool KV>
@@ -127,47 +226,22 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   const bool flip = 2 * (n - cnt) < n;
   auto mem = [&](uint64_t i) -> uint64_t { return flip ? n - 1 - i : i; };
   auto isp = [&](T x) -> bool { return flip ? (x > pivot) : (x <= pivot); };
-  auto swap_at = [&](uint64_t p, uint64_t q, T x, T y) {
-    A[p] = y;
-    A[q] = x;
-    if constexpr (KV) {
-      const uint64_t u = ldcg(&Y[p]), w = ldcg(&Y[q]);
-      Y[p] = w;
-      Y[q] = u;
-    }
-  };
 
-  // ---- 2. MakeSuccessorHeavy
+
+  // ---- 2. MakeSuccessorHeavy, kMshFuse levels per pass
   uint64_t m = n;
   while (m > 1) {
-    const uint64_t half = m / 2;
-    if (half >= kMshSmall) {
-      for (uint64_t i0 = gtid; i0 < half; i0 += kUnroll * gstride) {
-        T x[kUnroll], y[kUnroll];
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++) {
-          const uint64_t i = i0 + u * gstride;
-          if (i < half) { x[u] = ldcg(&A[mem(i)]); y[u] = ldcg(&A[mem(m - 1 - i)]); }
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++) {
-          const uint64_t i = i0 + u * gstride;
-          if (i < half && isp(x[u]) && !isp(y[u])) swap_at(mem(i), mem(m - 1 - i), x[u], y[u]);
-        }
-      }
+    const uint64_t mL = msh_after<kMshFuse<KV>>(m);
+    if (m / 2 >= kMshSmall) {
+      msh_pass<kMshFuse<KV>, T, KV>(A, Y, m, gtid, gstride, mem, isp);
       if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
-      m -= half;
+      m = mL;
     } else {
       if (blockIdx.x == 0) {
         while (m > 1) {
-          const uint64_t h2 = m / 2;
-          for (uint64_t i = tid; i < h2; i += kLT) {
-            const uint64_t p = mem(i), q = mem(m - 1 - i);
-            const T x = ldcg(&A[p]), y = ldcg(&A[q]);
-            if (isp(x) && !isp(y)) swap_at(p, q, x, y);
-          }
+          msh_pass<kMshFuse<KV>, T, KV>(A, Y, m, tid, kLT, mem, isp);
           __syncthreads();
-          m -= h2;
+          m = msh_after<kMshFuse<KV>>(m);
         }
       }
       m = 1;
@@ -185,35 +259,61 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     return;
   }
   if (nb > 0) {
+    // every CTA owns the blocks [b0, b1); its warps count one block each
+    // (kUnroll2 loads in flight per lane) into v[b], the CTA turns those
+    // counts into an inclusive prefix over its range, then adds the totals of
+    // the CTAs before it
     const uint64_t bpc = (nb + gridDim.x - 1) / gridDim.x;
     const uint64_t b0 = min((uint64_t)blockIdx.x * bpc, nb), b1 = min(b0 + bpc, nb);
-    unsigned long long run = 0;
-    for (uint64_t b = b0; b < b1; b++) {
+    unsigned long long* V = reinterpret_cast<unsigned long long*>(a.v);
+    for (uint64_t b = b0 + warp; b < b1; b += kLT / 32) {
       const uint64_t s = b * B, e = (b + 1 == nb) ? n : s + B;
-      unsigned long long c = 0;
-      for (uint64_t q0 = s + tid; q0 < e; q0 += (uint64_t)kUnroll * kLT) {
-        T x[kUnroll];
+      uint32_t c = 0;
+      for (uint64_t q0 = s + lane; q0 < e; q0 += 32ull * kUnroll2) {
+        T x[kUnroll2];
 #pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++) {
-          const uint64_t q = q0 + (uint64_t)u * kLT;
+        for (uint32_t u = 0; u < kUnroll2; u++) {
+          const uint64_t q = q0 + 32ull * u;
           if (q < e) x[u] = ldcg(&A[mem(q)]);
         }
 #pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++)
-          c += (q0 + (uint64_t)u * kLT < e && isp(x[u])) ? 1u : 0u;
+        for (uint32_t u = 0; u < kUnroll2; u++)
+          c += (q0 + 32ull * u < e && isp(x[u])) ? 1u : 0u;
       }
-      c = cta_sum(c, red);
-      run += c;
-      if (tid == 0) __stcg(reinterpret_cast<unsigned long long*>(&a.v[b]), run);
+      unsigned long long cw = c;  // a block may hold more than 2^32 keys
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
+      if (lane == 0) __stcg(&V[b], cw);
     }
-    if (tid == 0) __stcg(&a.cta[blockIdx.x], run);
+    __syncthreads();
+    // thread tid sums the counts [c0, c1) of its share of the range
+    const uint64_t per = (b1 - b0 + kLT - 1) / kLT;
+    const uint64_t c0 = min(b0 + tid * per, b1), c1 = min(c0 + per, b1);
+    unsigned long long own = 0;
+    for (uint64_t b = c0; b < c1; b++) own += __ldcg(&V[b]);
+    // exclusive scan of the shares across the CTA
+    unsigned long long incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long w = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += w;
+    }
+    __syncthreads();
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    unsigned long long before = incl - own;
+    for (uint32_t w = 0; w < warp; w++) before += red[w];
+    unsigned long long ctatot = 0;
+    for (uint32_t w = 0; w < kLT / 32; w++) ctatot += red[w];
+    if (tid == 0) __stcg(&a.cta[blockIdx.x], ctatot);
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
     unsigned long long off = 0;
     for (uint32_t c2 = tid; c2 < blockIdx.x; c2 += kLT) off += __ldcg(&a.cta[c2]);
     off = cta_sum(off, red);
-    for (uint64_t b = b0 + tid; b < b1; b += kLT) {
-      unsigned long long* pv = reinterpret_cast<unsigned long long*>(&a.v[b]);
-      __stcg(pv, __ldcg(pv) + off);
+    unsigned long long run = off + before;
+    for (uint64_t b = c0; b < c1; b++) {
+      run += __ldcg(&V[b]);
+      __stcg(&V[b], run);
     }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }
@@ -250,44 +350,90 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }
   stamp(4);
-  // Reorder level by level, outward; one warp per block, kUnroll rounds of 32
-  // keys in flight: every predecessor of block i goes to v[i-1] + its rank in
-  // the block (a successor inside the successor-heavy prefix), so the target
-  // loads of a group of rounds can all be issued before its stores
+  // Reorder level by level, outward; one warp per block, rounds of 32 * kRU
+  // keys: every predecessor of block i goes to v[i-1] + its rank in the block
+  // (a successor inside the successor-heavy prefix, which is partitioned
+  // already).  Blocks and their targets are disjoint, so the next round's
+  // keys (of this block or the warp's next one) load while this round's
+  // targets do.
+  constexpr uint32_t kRU = KV ? 4 : kUnroll;
   const uint64_t gwarp = ((uint64_t)blockIdx.x * kLT + tid) >> 5;
   const uint64_t nwarps = gstride >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  const unsigned long long* V = reinterpret_cast<const unsigned long long*>(a.v);
   for (int j = L - 1; j >= 0; j--) {
     const uint64_t M = levM[j], t0 = levT[j], NB = levNB[j];
-    for (uint64_t i = t0 + gwarp; i < NB; i += nwarps) {
-      const uint64_t s0 = i * B, e = (i + 1 == NB) ? M : s0 + B;
-      uint64_t y = __ldcg(reinterpret_cast<const unsigned long long*>(&a.v[i - 1]));
-      for (uint64_t r0 = s0; r0 < e; r0 += 32ull * kUnroll) {
-        T x[kUnroll], z[kUnroll];
-        uint64_t tg[kUnroll];
-        uint32_t f = 0, bal[kUnroll];
+    uint64_t i = t0 + gwarp;
+    if (i < NB) {
+      uint64_t r0 = i * B, e = (i + 1 == NB) ? M : r0 + B;
+      uint64_t y = __ldcg(&V[i - 1]);
+      T x[kRU];
 #pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++) {
-          const uint64_t q = r0 + 32ull * u + lane;
-          if (q < e) {
-            x[u] = ldcg(&A[mem(q)]);
-            f |= (isp(x[u]) ? 1u : 0u) << u;
-          }
+      for (uint32_t u = 0; u < kRU; u++) {
+        const uint64_t q = r0 + 32ull * u + lane;
+        if (q < e) x[u] = ldcg(&A[mem(q)]);
+      }
+      for (;;) {
+        // the next round: the rest of this block, else the warp's next block
+        uint64_t i1 = i, r1 = r0 + 32ull * kRU, e1 = e;
+        const bool next_block = r1 >= e;
+        if (next_block) {
+          i1 = i + nwarps;
+          r1 = i1 * B;
+          e1 = (i1 + 1 == NB) ? M : r1 + B;
         }
+        const bool more = i1 < NB;
+        uint32_t f = 0;
+#pragma unroll
+        for (uint32_t u = 0; u < kRU; u++)
+          f |= (r0 + 32ull * u + lane < e && isp(x[u]) ? 1u : 0u) << u;
+        T z[kRU];
+        uint32_t tg[kRU];  // target offsets from y
+        uint64_t py[KV ? kRU : 1], pz[KV ? kRU : 1];
         uint32_t run = 0;
 #pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++) {
-          bal[u] = __ballot_sync(0xffffffffu, (f >> u) & 1u);
+        for (uint32_t u = 0; u < kRU; u++) {
+          const uint32_t bal = __ballot_sync(0xffffffffu, (f >> u) & 1u);
+          tg[u] = run + __popc(bal & lt);
           if ((f >> u) & 1u) {
-            tg[u] = mem(y + run + __popc(bal[u] & lt));
-            z[u] = ldcg(&A[tg[u]]);
+            const uint64_t pt = mem(y + tg[u]);
+            z[u] = ldcg(&A[pt]);
+            if constexpr (KV) {
+              pz[u] = ldcg(&Y[pt]);
+              py[u] = ldcg(&Y[mem(r0 + 32ull * u + lane)]);
+            }
           }
-          run += __popc(bal[u]);
+          run += __popc(bal);
+        }
+        T xn[kRU];
+        uint64_t yn = y + run;
+        if (more) {
+#pragma unroll
+          for (uint32_t u = 0; u < kRU; u++) {
+            const uint64_t q = r1 + 32ull * u + lane;
+            if (q < e1) xn[u] = ldcg(&A[mem(q)]);
+          }
+          if (next_block) yn = __ldcg(&V[i1 - 1]);
         }
 #pragma unroll
-        for (uint32_t u = 0; u < kUnroll; u++)
-          if ((f >> u) & 1u) swap_at(tg[u], mem(r0 + 32ull * u + lane), z[u], x[u]);
-        y += run;
+        for (uint32_t u = 0; u < kRU; u++) {
+          if ((f >> u) & 1u) {
+            const uint64_t pt = mem(y + tg[u]), ps = mem(r0 + 32ull * u + lane);
+            A[pt] = x[u];
+            A[ps] = z[u];
+            if constexpr (KV) {
+              Y[pt] = py[u];
+              Y[ps] = pz[u];
+            }
+          }
+        }
+        if (!more) break;
+#pragma unroll
+        for (uint32_t u = 0; u < kRU; u++) x[u] = xn[u];
+        i = i1;
+        r0 = r1;
+        e = e1;
+        y = yn;
       }
     }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
