@@ -22,14 +22,21 @@ struct Coop {
 // predecessors; after a grid barrier each CTA knows the predecessors of the
 // blocks before it and writes its predecessors, then its successors, to their
 // final places (stable).  Every key is read once and written once.  All threads
-// of all CTAs call this.  Returns the predecessor count of the range, or
-// ~0 if this CTA gave up at the grid barrier.
-template <typename T, bool KV>
+// of all CTAs call this, and a CTA has exactly NT threads (the per-warp sums
+// take 3 * NT/32 words).  Returns the predecessor count of the range, or ~0
+// if this CTA gave up at the grid barrier or was launched with another
+// thread count.
+template <typename T, bool KV, uint32_t NT = Tr<T, KV>::Threads>
 __device__ uint64_t coop_finish(T* __restrict__ base, uint64_t* __restrict__ vbase, uint64_t n,
                                 T pivot, const TaskScratch& S, unsigned char* smem,
                                 unsigned int* flag) {
-  constexpr uint32_t NT = Tr<T, KV>::Threads, A = Tr<T, KV>::A;
-  uint32_t* wsum = reinterpret_cast<uint32_t*>(smem);  // 2 * NT/32 words
+  constexpr uint32_t A = Tr<T, KV>::A;
+  static_assert(NT % 32 == 0 && 3 * (NT / 32) * 4 <= 128, "per-warp sums fit 128 bytes");
+  if (blockDim.x != NT) {  // same in every CTA: all of them leave here
+    if (threadIdx.x == 0) atomicOr(S.status, kStatRing);
+    return ~0ull;
+  }
+  uint32_t* wsum = reinterpret_cast<uint32_t*>(smem);  // 3 * NT/32 words
   T* sk = reinterpret_cast<T*>(smem + 128);
   uint64_t* sv = reinterpret_cast<uint64_t*>(smem + 128 + (size_t)Coop<T, KV>::Keys * sizeof(T));
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;

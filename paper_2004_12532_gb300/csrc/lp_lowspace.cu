@@ -38,7 +38,6 @@ namespace {
 constexpr uint32_t kLT = 256;               // threads per CTA
 constexpr uint64_t kMshSmall = 1u << 15;    // pair counts below this: one CTA
 constexpr uint32_t kUnroll = 8;             // independent loads in flight per thread
-constexpr uint32_t kUnroll2 = 16;           // the same, where a lane has nothing else to hold
 constexpr int kMaxReorderLevels = 96;
 
 struct LowArgs {
@@ -73,6 +72,43 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long x,
   unsigned long long s = 0;
   for (uint32_t w = 0; w < kLT / 32; w++) s += red[w];
   return s;
+}
+
+// Predecessor count of the memory positions [p0, p1) of A, order being
+// irrelevant: 16-byte loads (kUnroll per thread in flight) for the aligned
+// body, single keys for the head and tail.  Thread `start` of `stride`
+// threads takes its share; the caller sums the shares.
+template <typename T, typename Isp>
+__device__ __forceinline__ uint32_t count_span(const T* A, uint64_t p0, uint64_t p1,
+                                               uint64_t start, uint64_t stride, const Isp& isp) {
+  constexpr uint32_t E = 16 / sizeof(T);
+  const uint64_t len = p1 - p0;
+  uint64_t head = ((16u - ((uintptr_t)(A + p0) & 15u)) & 15u) / sizeof(T);
+  if (head > len) head = len;
+  const uint64_t nv = (len - head) / E;
+  const uint4* vb = reinterpret_cast<const uint4*>(A + p0 + head);
+  uint32_t c = 0;
+  for (uint64_t v0 = start; v0 < nv; v0 += kUnroll * stride) {
+    uint4 w[kUnroll];
+#pragma unroll
+    for (uint32_t u = 0; u < kUnroll; u++)
+      if (v0 + u * stride < nv) w[u] = __ldcg(vb + v0 + u * stride);
+#pragma unroll
+    for (uint32_t u = 0; u < kUnroll; u++) {
+      if (v0 + u * stride >= nv) continue;
+      if constexpr (sizeof(T) == 8) {
+        c += isp((T)(((uint64_t)w[u].y << 32) | w[u].x)) ? 1u : 0u;
+        c += isp((T)(((uint64_t)w[u].w << 32) | w[u].z)) ? 1u : 0u;
+      } else {
+        c += (isp((T)w[u].x) ? 1u : 0u) + (isp((T)w[u].y) ? 1u : 0u) +
+             (isp((T)w[u].z) ? 1u : 0u) + (isp((T)w[u].w) ? 1u : 0u);
+      }
+    }
+  }
+  const uint64_t t0 = p0 + head + nv * E, rest = head + (p1 - t0);
+  for (uint64_t q = start; q < rest; q += stride)
+    c += isp(ldcg(&A[q < head ? p0 + q : t0 + (q - head)])) ? 1u : 0u;
+  return c;
 }
 
 // MakeSuccessorHeavy level k works on the prefix of m_k keys: it pairs i with
@@ -203,18 +239,8 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
 
   // ---- 1. count, role swap
   {
-    unsigned long long c = 0;
-    for (uint64_t q0 = gtid; q0 < n; q0 += kUnroll * gstride) {  // kUnroll loads in flight
-      T x[kUnroll];
-#pragma unroll
-      for (uint32_t u = 0; u < kUnroll; u++) {
-        const uint64_t q = q0 + u * gstride;
-        x[u] = q < n ? ldcg(&A[q]) : pivot;
-      }
-#pragma unroll
-      for (uint32_t u = 0; u < kUnroll; u++)
-        c += (q0 + u * gstride < n && x[u] <= pivot) ? 1u : 0u;
-    }
+    unsigned long long c =
+        count_span(A, 0, n, gtid, gstride, [&](T x) { return x <= pivot; });
     c = cta_sum(c, red);
     if (tid == 0) atomicAdd(a.total, c);
   }
@@ -260,7 +286,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   }
   if (nb > 0) {
     // every CTA owns the blocks [b0, b1); its warps count one block each
-    // (kUnroll2 loads in flight per lane) into v[b], the CTA turns those
+    // (16-byte loads) into v[b], the CTA turns those
     // counts into an inclusive prefix over its range, then adds the totals of
     // the CTAs before it
     const uint64_t bpc = (nb + gridDim.x - 1) / gridDim.x;
@@ -268,18 +294,8 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     unsigned long long* V = reinterpret_cast<unsigned long long*>(a.v);
     for (uint64_t b = b0 + warp; b < b1; b += kLT / 32) {
       const uint64_t s = b * B, e = (b + 1 == nb) ? n : s + B;
-      uint32_t c = 0;
-      for (uint64_t q0 = s + lane; q0 < e; q0 += 32ull * kUnroll2) {
-        T x[kUnroll2];
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll2; u++) {
-          const uint64_t q = q0 + 32ull * u;
-          if (q < e) x[u] = ldcg(&A[mem(q)]);
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll2; u++)
-          c += (q0 + 32ull * u < e && isp(x[u])) ? 1u : 0u;
-      }
+      const uint32_t c = flip ? count_span(A, n - e, n - s, lane, 32, isp)
+                              : count_span(A, s, e, lane, 32, isp);
       unsigned long long cw = c;  // a block may hold more than 2^32 keys
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
@@ -344,8 +360,8 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     // the innermost prefix, partitioned on chip: in memory it is [0, mbase)
     // or, for the reversed view, [n - mbase, n) with the roles back in place
     const uint64_t off = flip ? n - mbase : 0;
-    const uint64_t t = coop_finish<T, KV>(A + off, KV ? Y + off : nullptr, mbase, pivot, S,
-                                          smem_raw, &flag);
+    const uint64_t t = coop_finish<T, KV, kLT>(A + off, KV ? Y + off : nullptr, mbase, pivot,
+                                               S, smem_raw, &flag);
     if (t == ~0ull) { fail(); return; }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }

@@ -95,3 +95,27 @@ def test_strided_adversarial_period(ctx):
     dev = to_dev(host)
     t = lp.lp_partition_u64(ctx, dev, 5, lp.LP_STRIDED)
     check_partition(to_host(dev, np.uint64), host, t, oracle.count(host, 5), 5)
+
+
+@pytest.mark.parametrize("variant", [lp.LP_LOWSPACE, lp.LP_STRIDED, lp.LP_HYBRID])
+@pytest.mark.parametrize("frac", [(1, 3), (1, 2), (7, 10)])
+def test_variants_kv_repeated(ctx, variant, frac):
+    """Key + payload through the low-space kernel with the predecessors the
+    minority, about half, and the majority (the reversed view), 12 seeded
+    inputs each: a fault that depends on timing between CTAs (two warps
+    writing one shared-memory word) shows up as duplicated key/payload pairs."""
+    pv = inputs.quantile_pivot(*frac)
+    flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    p_signed = pv - (1 << 63)
+    for r in range(12):
+        n = (1 << 22) + 3 + 1000 * r
+        keys = torch.empty(n, dtype=torch.int64, device="cuda")
+        lp.lp_fill_uniform_u64(keys, 7000 + 31 * r + variant)
+        kin = keys.clone()
+        vals = torch.arange(n, dtype=torch.int64, device="cuda")
+        t = lp.lp_partition_kv_u64(ctx, keys, vals, pv, variant, seed=r)
+        ki, ko = kin ^ flip, keys ^ flip  # signed order of the flipped bits = unsigned order
+        assert t == int((ki <= p_signed).sum())
+        assert int((ko[:t] > p_signed).sum()) == 0 and int((ko[t:] <= p_signed).sum()) == 0
+        assert torch.equal(torch.sort(kin)[0], torch.sort(keys)[0])  # a permutation
+        assert torch.equal(kin[vals], keys)  # every payload still names its key
