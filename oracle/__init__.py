@@ -41,6 +41,11 @@ def lib():
             "or_block_prefix_u64": (_u64, [_p, _u64, _u64, C.c_int, _u64, _p]),
             "or_reorder_u64": (None, [_p, _u64, _u64, C.c_int, _u64, _p]),
             "or_lowspace_partition_u64": (_u64, [_p, _u64, _u64, _u64]),
+            "or_bits_for": (_u64, [_u64]),
+            "or_bitstore_encode_u64": (None, [_p, _u64, _u64, C.c_int]),
+            "or_bitstore_decode_u64": (_u64, [_p, _u64, C.c_int]),
+            "or_implicit_prefix_u64": (_u64, [_p, _u64, _u64, _u64, _p]),
+            "or_implicit_partition_u64": (_u64, [_p, _u64, _u64, _u64]),
             "or_quicksort_u64": (None, [_p, _u64, _u64]),
             "or_quicksort_u32": (None, [_p, _u64, _u64]),
         }
@@ -165,6 +170,36 @@ def reorder(a, pivot, B, v, flip=0):
 def lowspace_partition(a, pivot, B=4096):
     _check(a, np.uint64)
     return int(lib().or_lowspace_partition_u64(_ptr(a), a.size, int(pivot), B))
+
+
+def bits_for(n):
+    return int(lib().or_bits_for(n))
+
+
+def bitstore_encode(x, L, v, first):
+    """Encode v in x[:4L+2] (modified in place)."""
+    _check(x, np.uint64)
+    assert x.size >= 4 * L + 2
+    lib().or_bitstore_encode_u64(_ptr(x), L, int(v), 1 if first else 0)
+
+
+def bitstore_decode(x, L, restore=True):
+    _check(x, np.uint64)
+    assert x.size >= 4 * L + 2
+    return int(lib().or_bitstore_decode_u64(_ptr(x), L, 1 if restore else 0))
+
+
+def implicit_prefix(a, pivot, B):
+    """Returns (t, flip); a is left with every block's value encoded."""
+    _check(a, np.uint64)
+    f = C.c_int(0)
+    t = int(lib().or_implicit_prefix_u64(_ptr(a), a.size, int(pivot), B, C.byref(f)))
+    return t, int(f.value)
+
+
+def implicit_partition(a, pivot, B):
+    _check(a, np.uint64)
+    return int(lib().or_implicit_partition_u64(_ptr(a), a.size, int(pivot), B))
 
 
 def quicksort(a, seed=0):

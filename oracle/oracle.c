@@ -345,6 +345,184 @@ uint64_t or_lowspace_partition_u64(uint64_t *a, uint64_t n, uint64_t pivot, uint
 }
 
 /* ------------------------------------------------------------------ */
+/* Sec. 3, fully in place: the prefix values are kept in the order of the
+ * keys of each block (Lemma bitstore2, which allows repeated keys), not in
+ * an array.  L = ceil(log2(n + 1)) bits hold a value in [0, n]; the first
+ * 4L + 2 keys of a block are read as 2L + 1 adjacent pairs.                 */
+uint64_t or_bits_for(uint64_t n)
+{
+    uint64_t L = 0;
+    while (L < 64 && (n >> L) != 0) L++; /* the bit length of n */
+    return L;
+}
+
+/* Pair k of the block starting at s: positions s + 2k and s + 2k + 1. */
+static void swap_pairs(const view_t *w, uint64_t s, uint64_t j, uint64_t k)
+{
+    vswap(w, s + 2 * j, s + 2 * k);
+    vswap(w, s + 2 * j + 1, s + 2 * k + 1);
+}
+
+/* Encode v in the block at s.  On the first call the pairs are reordered
+ * (keeping their relative order) so that the kind of pair that makes up at
+ * least half of the 2L + 1 pairs comes first: unequal pairs (L + 1 or more)
+ * give the first kind, where pair k < L holds bit k of v in its order
+ * (first key > second key <=> 1); otherwise equal pairs come first, and the
+ * second key of pair k, 1 <= k <= L, is overwritten with bit k - 1 of v.
+ * Pair 0 tells the kinds apart: unequal for the first, equal for the second. */
+static void bitstore_encode(const view_t *w, uint64_t s, uint64_t L, uint64_t v, int first)
+{
+    const uint64_t P = 2 * L + 1;
+    if (first) {
+        uint64_t unequal = 0;
+        for (uint64_t k = 0; k < P; k++)
+            if (*at(w, s + 2 * k) != *at(w, s + 2 * k + 1)) unequal++;
+        const int want_unequal = unequal >= L + 1;
+        /* stable: bubble every wanted pair down to the next free front slot */
+        uint64_t front = 0;
+        for (uint64_t k = 0; k < P; k++) {
+            const int uneq = *at(w, s + 2 * k) != *at(w, s + 2 * k + 1);
+            if (uneq == want_unequal) {
+                for (uint64_t j = k; j > front; j--) swap_pairs(w, s, j - 1, j);
+                front++;
+            }
+        }
+    }
+    if (*at(w, s) != *at(w, s + 1)) {
+        for (uint64_t k = 0; k < L; k++) {
+            uint64_t *x = at(w, s + 2 * k), *y = at(w, s + 2 * k + 1);
+            const int bit = (int)((v >> k) & 1);
+            const int desc = *x > *y;
+            if (desc != bit) { uint64_t t = *x; *x = *y; *y = t; }
+        }
+    } else {
+        for (uint64_t k = 1; k <= L; k++) *at(w, s + 2 * k + 1) = (v >> (k - 1)) & 1;
+    }
+}
+
+/* Decode the value of the block at s; with restore, put back the keys the
+ * second kind overwrote (each equals the first key of its pair).          */
+static uint64_t bitstore_decode(const view_t *w, uint64_t s, uint64_t L, int restore)
+{
+    uint64_t v = 0;
+    if (*at(w, s) != *at(w, s + 1)) {
+        for (uint64_t k = 0; k < L; k++)
+            if (*at(w, s + 2 * k) > *at(w, s + 2 * k + 1)) v |= 1ull << k;
+    } else {
+        for (uint64_t k = 1; k <= L; k++) {
+            if (*at(w, s + 2 * k + 1) != 0) v |= 1ull << (k - 1);
+            if (restore) *at(w, s + 2 * k + 1) = *at(w, s + 2 * k);
+        }
+    }
+    return v;
+}
+
+void or_bitstore_encode_u64(uint64_t *x, uint64_t L, uint64_t v, int first)
+{
+    view_t w = {x, 4 * L + 2, 0, 0};
+    bitstore_encode(&w, 0, L, v, first);
+}
+
+uint64_t or_bitstore_decode_u64(uint64_t *x, uint64_t L, int restore)
+{
+    view_t w = {x, 4 * L + 2, 0, 0};
+    return bitstore_decode(&w, 0, L, restore);
+}
+
+/* The in-place prefix sum on values v_1..v_m kept in blocks (1-indexed, the
+ * k-th value in block stride * k - 1): v_{2i} += v_{2i-1}; recurse on the
+ * even-indexed values; v_{2i+1} += v_{2i}.                                  */
+static void implicit_prefix_rec(const view_t *w, uint64_t B, uint64_t L, uint64_t stride,
+                                uint64_t m)
+{
+    if (m <= 1) return;
+#define BLK(k) (((k) * stride - 1) * B)
+    for (uint64_t k = 2; k <= m; k += 2) {
+        const uint64_t a = bitstore_decode(w, BLK(k - 1), L, 0);
+        const uint64_t b = bitstore_decode(w, BLK(k), L, 0);
+        bitstore_encode(w, BLK(k), L, a + b, 0);
+    }
+    implicit_prefix_rec(w, B, L, 2 * stride, m / 2);
+    for (uint64_t k = 3; k <= m; k += 2) {
+        const uint64_t a = bitstore_decode(w, BLK(k - 1), L, 0);
+        const uint64_t b = bitstore_decode(w, BLK(k), L, 0);
+        bitstore_encode(w, BLK(k), L, a + b, 0);
+    }
+#undef BLK
+}
+
+/* The prefix phase: each block first stores its own predecessor count, the
+ * in-place prefix sum makes that the count in blocks 1..i, and a last pass
+ * from the end moves each value one block on, so that block i ends with the
+ * predecessors before it -- the value the reordering phase adds each
+ * predecessor's rank to.  Returns the number of blocks floor(m/B).         */
+static uint64_t implicit_prefix_view(const view_t *w, uint64_t B, uint64_t L)
+{
+    const uint64_t nb = w->n / B;
+    for (uint64_t i = 0; i < nb; i++) {
+        const uint64_t start = i * B, end = (i + 1 == nb) ? w->n : start + B;
+        uint64_t c = 0;
+        for (uint64_t p = start; p < end; p++)
+            if (is_pred(w, *at(w, p))) c++;
+        bitstore_encode(w, start, L, c, 1);
+    }
+    implicit_prefix_rec(w, B, L, 1, nb);
+    for (uint64_t i = nb; i-- > 1;)
+        bitstore_encode(w, i * B, L, bitstore_decode(w, (i - 1) * B, L, 0), 0);
+    if (nb > 0) bitstore_encode(w, 0, L, 0, 0);
+    return nb;
+}
+
+/* Count, role swap, MakeSuccessorHeavy and the prefix phase; the array is
+ * left with every block's value encoded.  Returns t; *flip gets the role. */
+uint64_t or_implicit_prefix_u64(uint64_t *a, uint64_t n, uint64_t pivot, uint64_t B, int *flip)
+{
+    const uint64_t t = or_count_u64(a, n, pivot);
+    const int f = 2 * (n - t) < n ? 1 : 0;
+    if (flip) *flip = f;
+    if (n == 0) return 0;
+    view_t w = {a, n, pivot, f};
+    msh_view(&w, n);
+    implicit_prefix_view(&w, B, or_bits_for(n));
+    return t;
+}
+
+/* Reordering with the values read from the blocks (restoring overwritten
+ * keys as each block is read); the base case first restores the blocks of
+ * the prefix, then partitions it serially.                                */
+static void implicit_reorder_view(const view_t *w, uint64_t m, uint64_t B, uint64_t L)
+{
+    const uint64_t nb = m / B;
+    const uint64_t t = (4 * m + 5 * B - 1) / (5 * B);
+    if (m <= 5 * B || t >= nb) {
+        for (uint64_t i = 0; i < nb; i++) bitstore_decode(w, i * B, L, 1);
+        serial_partition_view(w, m);
+        return;
+    }
+    implicit_reorder_view(w, t * B, B, L);
+    for (uint64_t i = t; i < nb; i++) {
+        const uint64_t start = i * B, end = (i + 1 == nb) ? m : start + B;
+        uint64_t y = bitstore_decode(w, start, L, 1); /* predecessors before X_i */
+        for (uint64_t p = start; p < end; p++) {
+            if (is_pred(w, *at(w, p))) {
+                vswap(w, p, y);
+                y++;
+            }
+        }
+    }
+}
+
+uint64_t or_implicit_partition_u64(uint64_t *a, uint64_t n, uint64_t pivot, uint64_t B)
+{
+    int flip = 0;
+    const uint64_t t = or_implicit_prefix_u64(a, n, pivot, B, &flip);
+    if (n == 0) return 0;
+    view_t w = {a, n, pivot, flip};
+    implicit_reorder_view(&w, n, B, or_bits_for(n));
+    return t;
+}
+
+/* ------------------------------------------------------------------ */
 /* Quicksort on the partition (Sec. 5, "A Full Quicksort").  Pivot = median
  * of three seeded samples of the subarray.  When every key of the subarray is
  * <= pivot, a second partition by [x < pivot] peels off the keys equal to the

@@ -91,6 +91,22 @@ void or_reorder_u64(uint64_t *a, uint64_t n, uint64_t pivot, int flip, uint64_t 
  * Returns t. */
 uint64_t or_lowspace_partition_u64(uint64_t *a, uint64_t n, uint64_t pivot, uint64_t B);
 
+/* --- Blocked-Prefix-Sum partition, values kept in key order (Sec. 3,
+ * Lemma bitstore2; parity pinned by the round trip, brute-force prefixes
+ * and the partition postcondition) --- */
+/* L = ceil(log2(n + 1)), the bits of a value in [0, n]. */
+uint64_t or_bits_for(uint64_t n);
+/* Encode v (< 2^L) in x[0 .. 4L+2); first = 1 on the first call for x. */
+void or_bitstore_encode_u64(uint64_t *x, uint64_t L, uint64_t v, int first);
+/* Decode the value of x[0 .. 4L+2); restore = 1 puts back overwritten keys. */
+uint64_t or_bitstore_decode_u64(uint64_t *x, uint64_t L, int restore);
+/* Count, role swap, MakeSuccessorHeavy, then the prefix phase with block i
+ * encoding the predecessors before it (blocks of B >= 4L + 2 keys, the last
+ * taking the remainder).  Returns t; *flip gets the role (may be NULL). */
+uint64_t or_implicit_prefix_u64(uint64_t *a, uint64_t n, uint64_t pivot, uint64_t B, int *flip);
+/* The whole fully in-place partition.  Returns t. */
+uint64_t or_implicit_partition_u64(uint64_t *a, uint64_t n, uint64_t pivot, uint64_t B);
+
 /* --- quicksort on the partition (Sec. 5, "A Full Quicksort") --- */
 void or_quicksort_u64(uint64_t *a, uint64_t n, uint64_t seed);
 void or_quicksort_u32(uint32_t *a, uint64_t n, uint64_t seed);
