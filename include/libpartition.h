@@ -374,6 +374,40 @@ lp_status lp_lowspace_partition_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uin
                                     uint64_t B, uint64_t base_keys, cudaStream_t stream,
                                     uint64_t *split_out);
 
+/* ------------------------- Blocked-Prefix-Sum partition, values in key order
+ * The fully in-place form of Sec. 3 (An Implicit Parallel Prefix Sum; In-Place
+ * Reordering; Lemma bitstore2, which allows repeated keys): the same phases as
+ * lp_lowspace_partition_*, but block i keeps the number of predecessors
+ * before it in the order of its own first 4L + 2 keys (L = ceil(log2(n+1))),
+ * not in a counter array.  Of its 2L + 1 adjacent pairs, the first write
+ * moves the more common kind first (keeping their order): unequal pairs hold
+ * one bit each in their order (first > second <=> 1); otherwise the second
+ * keys of equal pairs 1..L are overwritten with the bits and are put back
+ * when the block is read.  Auxiliary device memory: 8 bytes per CTA plus the
+ * context's fixed words, whatever n.
+ * B: block size, at least 4L + 2 (0 selects exactly 4L + 2, the paper's
+ * size); n < 2^40.  base_keys as in lp_lowspace_partition_*.  Keys only.
+ * Errors: LP_ERR_INVALID_ARG for a null or misaligned array with n > 0, a
+ * null split_out, B below 4L + 2 or n >= 2^40.  *split_out (host) receives
+ * t; synchronises `stream`. */
+lp_status lp_lowspace_implicit_partition_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n,
+                                             uint64_t pivot, uint64_t B, uint64_t base_keys,
+                                             cudaStream_t stream, uint64_t *split_out);
+lp_status lp_lowspace_implicit_partition_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n,
+                                             uint32_t pivot, uint64_t B, uint64_t base_keys,
+                                             cudaStream_t stream, uint64_t *split_out);
+/* The first three phases only (count and role swap, MakeSuccessorHeavy, the
+ * prefix phase): keys[0..n) is left as the reordering phase would find it,
+ * every block's value encoded in its keys, in the logical order of the role
+ * (reversed when the predecessors are the majority, 2(n - t) < n).  Exposes
+ * the intermediate state; same arguments and errors as above. */
+lp_status lp_lowspace_implicit_prefix_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n,
+                                          uint64_t pivot, uint64_t B, cudaStream_t stream,
+                                          uint64_t *split_out);
+lp_status lp_lowspace_implicit_prefix_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n,
+                                          uint32_t pivot, uint64_t B, cudaStream_t stream,
+                                          uint64_t *split_out);
+
 /* ------------------------------------------------- one Partial Partition Step
  * Runs exactly one Partial Partition Step (Sec. 4, "Formal Algorithm
  * Description"; Proposition 4.2) on keys[0..n) with explicit parameters:

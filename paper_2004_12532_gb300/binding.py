@@ -111,6 +111,10 @@ _SIGS = {
     "lp_partition_u64_noalloc": (_i, [_p, _u64, _u64, _i, _u64, _p, _p]),
     "lp_lowspace_partition_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _p, _pu64]),
     "lp_lowspace_partition_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _p, _pu64]),
+    "lp_lowspace_implicit_partition_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _p, _pu64]),
+    "lp_lowspace_implicit_partition_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _p, _pu64]),
+    "lp_lowspace_implicit_prefix_u64": (_i, [_p, _p, _u64, _u64, _u64, _p, _pu64]),
+    "lp_lowspace_implicit_prefix_u32": (_i, [_p, _p, _u64, _u32, _u64, _p, _pu64]),
     "lp_partition_batched_u64": (_i, [_p, _p, _u32, _u64, _p, _p]),
     "lp_batch_create": (_i, [_p, _p, _u32, _u64, _p, _p, C.POINTER(_p)]),
     "lp_batch_launch": (_i, [_p, _p]),
@@ -429,6 +433,30 @@ def lp_lowspace_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):
     f = lib().lp_lowspace_partition_u64 if bits == 64 else lib().lp_lowspace_partition_u32
     t = C.c_uint64()
     ctx.check(f(ctx.h, p, n, int(pivot), int(B), int(base_keys), _stream(stream), C.byref(t)))
+    return int(t.value)
+
+
+def lp_lowspace_implicit_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):
+    """Blocked-Prefix-Sum partition with the block values kept in key order
+    (B = 0: the paper's 4 * ceil(log2(n + 1)) + 2); returns the split t."""
+    bits = keys.element_size() * 8
+    p, n = _dev_ptr(keys, bits)
+    f = (lib().lp_lowspace_implicit_partition_u64 if bits == 64
+         else lib().lp_lowspace_implicit_partition_u32)
+    t = C.c_uint64()
+    ctx.check(f(ctx.h, p, n, int(pivot), int(B), int(base_keys), _stream(stream), C.byref(t)))
+    return int(t.value)
+
+
+def lp_lowspace_implicit_prefix(ctx, keys, pivot, B=4096, stream=None):
+    """The first three phases of the above (keys left with the values
+    encoded); returns t."""
+    bits = keys.element_size() * 8
+    p, n = _dev_ptr(keys, bits)
+    f = (lib().lp_lowspace_implicit_prefix_u64 if bits == 64
+         else lib().lp_lowspace_implicit_prefix_u32)
+    t = C.c_uint64()
+    ctx.check(f(ctx.h, p, n, int(pivot), int(B), _stream(stream), C.byref(t)))
     return int(t.value)
 
 

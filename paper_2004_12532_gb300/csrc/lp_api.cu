@@ -254,6 +254,42 @@ lp_status lowspace_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t B, uin
   return read_back(c, stream, split_out);
 }
 
+template <typename T>
+lp_status implicit_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t B, uint64_t base_keys,
+                        int prefix_only, cudaStream_t stream, uint64_t* split_out) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->err.clear();
+  c->last_launches = 0;
+  if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
+  if (n > 0 && !keys) return fail(c, LP_ERR_INVALID_ARG, "null array");
+  if (!aligned_to(keys, sizeof(T))) return fail(c, LP_ERR_INVALID_ARG, "array not aligned");
+  const uint32_t L = lp::lowspace_value_bits(n);
+  if (L > lp::lowspace_value_bits_max())
+    return fail(c, LP_ERR_INVALID_ARG, "range too large for values kept in key order");
+  if (B == 0) B = 4ull * L + 2;  // the paper's block size
+  if (B < 4ull * L + 2)
+    return fail(c, LP_ERR_INVALID_ARG, "block size below 4 * ceil(log2(n + 1)) + 2");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  if (n == 0) { *split_out = 0; return LP_OK; }
+  lp::LaunchCfg cfg{sizeof(T) == 8 ? c->grid_u64 : c->grid_u32, stream, 0, nullptr};
+  c->last_timed = false;
+  c->last_stream = stream;
+  lp_status ls = ensure_var(c, lp::lowspace_implicit_scratch_bytes(cfg.grid), stream);
+  if (ls != LP_OK) return ls;
+  lp::TaskScratch S = c->task;
+  c->last_low_tl = nullptr;
+  cfg.phase_stamps = &c->last_low_tl;
+  e = cudaMemsetAsync(S.status, 0, 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.bar, 0, 8, stream);
+  if (e == cudaSuccess)
+    e = lp::launch_lowspace_implicit<T>(keys, n, pivot, B, base_keys ? base_keys : 1,
+                                        prefix_only, c->d_var, S, S.split, cfg);
+  c->last_launches = cfg.launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "launch");
+  return read_back(c, stream, split_out);
+}
+
 }  // namespace
 
 extern "C" {
@@ -448,6 +484,25 @@ lp_status lp_lowspace_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint3
                                     uint64_t B, uint64_t base_keys, cudaStream_t s,
                                     uint64_t* split_out) {
   return lowspace_impl<uint32_t>(c, keys, n, pivot, B, base_keys, s, split_out);
+}
+
+lp_status lp_lowspace_implicit_partition_u64(lp_ctx* c, uint64_t* keys, uint64_t n,
+                                             uint64_t pivot, uint64_t B, uint64_t base_keys,
+                                             cudaStream_t s, uint64_t* split_out) {
+  return implicit_impl<uint64_t>(c, keys, n, pivot, B, base_keys, 0, s, split_out);
+}
+lp_status lp_lowspace_implicit_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n,
+                                             uint32_t pivot, uint64_t B, uint64_t base_keys,
+                                             cudaStream_t s, uint64_t* split_out) {
+  return implicit_impl<uint32_t>(c, keys, n, pivot, B, base_keys, 0, s, split_out);
+}
+lp_status lp_lowspace_implicit_prefix_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
+                                          uint64_t B, cudaStream_t s, uint64_t* split_out) {
+  return implicit_impl<uint64_t>(c, keys, n, pivot, B, 0, 1, s, split_out);
+}
+lp_status lp_lowspace_implicit_prefix_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
+                                          uint64_t B, cudaStream_t s, uint64_t* split_out) {
+  return implicit_impl<uint32_t>(c, keys, n, pivot, B, 0, 1, s, split_out);
 }
 
 lp_status lp_fill_uniform_u64(uint64_t* d, uint64_t n, uint64_t seed, cudaStream_t s) {

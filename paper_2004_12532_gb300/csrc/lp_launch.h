@@ -55,6 +55,20 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
                             const LevelDesc* range_desc, T pivot, uint64_t B, uint64_t base_keys,
                             void* var, const TaskScratch& S, uint64_t* split, LaunchCfg& cfg);
 
+// The same partition with the block values kept in the order of each block's
+// keys (Sec. 3, Lemma bitstore2) instead of counters: keys[0..n), keys only;
+// B >= 4 * lowspace_value_bits(n) + 2 and lowspace_value_bits(n) <=
+// lowspace_value_bits_max().  prefix_only != 0 stops after the prefix phase,
+// leaving every block's value encoded.  `var` holds
+// lowspace_implicit_scratch_bytes(grid) bytes.
+size_t lowspace_implicit_scratch_bytes(uint32_t grid);
+uint32_t lowspace_value_bits(uint64_t n);
+uint32_t lowspace_value_bits_max();
+template <typename T>
+cudaError_t launch_lowspace_implicit(T* keys, uint64_t n, T pivot, uint64_t B,
+                                     uint64_t base_keys, int prefix_only, void* var,
+                                     const TaskScratch& S, uint64_t* split, LaunchCfg& cfg);
+
 // Smoothed Striding level 0 only (the Strided Algorithm's partial step when
 // strided != 0), leaving [vmin, vmax) in S.desc[0] for a cleanup; then
 // finalize_smoothed places the unaligned head and tail and writes the split.

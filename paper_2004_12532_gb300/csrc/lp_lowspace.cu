@@ -52,6 +52,7 @@ struct LowArgs {
   unsigned long long* total;       // predecessor count of the range
   uint64_t* split;                 // if set: the split (count) is written here
   unsigned long long* tl;          // device timestamps: start, then the end of each phase
+  int prefix_only;                 // values kept in key order: stop after the prefix phase
 };
 
 template <typename T>
@@ -206,9 +207,125 @@ __device__ __forceinline__ void msh_pass(T* A, uint64_t* Y, uint64_t m, uint64_t
   }
 }
 
-template <typename T, bool KV>
+// ---- Values kept in the order of a block's keys (Sec. 3, Lemma bitstore2).
+// L = bit length of the range size; the first 4L + 2 keys of a block (at
+// logical position s) are 2L + 1 adjacent pairs.  The first write reorders
+// the pairs, keeping their relative order, so that the kind making up at
+// least half of them comes first: unequal pairs (at least L + 1) hold bit k
+// of the value in the order of pair k < L (first > second <=> 1); otherwise
+// the second key of equal pair k, 1 <= k <= L, is overwritten with bit k - 1.
+// Pair 0 tells the kinds apart.  One warp per block; pair p = lane + 32 w.
+constexpr uint32_t kMaxValueBits = 40;          // ranges below 2^40 keys
+constexpr uint32_t kPairWords = (2 * kMaxValueBits + 1 + 31) / 32;
+
+// The first write of v into the block at s.
+template <typename T, typename Mem>
+__device__ __forceinline__ void warp_value_first(T* A, uint64_t s, uint32_t L, uint64_t v,
+                                                 const Mem& mem) {
+  const uint32_t lane = threadIdx.x & 31u, P = 2 * L + 1, lt = (1u << lane) - 1u;
+  T a[kPairWords], b[kPairWords];
+  uint32_t uneq[kPairWords], inm[kPairWords], nuneq = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kPairWords; w++) {
+    const uint32_t p = lane + 32 * w;
+    if (p < P) {
+      a[w] = ldcg(&A[mem(s + 2 * p)]);
+      b[w] = ldcg(&A[mem(s + 2 * p + 1)]);
+    }
+    inm[w] = __ballot_sync(0xffffffffu, p < P);
+    uneq[w] = __ballot_sync(0xffffffffu, p < P && a[w] != b[w]);
+    nuneq += __popc(uneq[w]);
+  }
+  const bool order_kind = nuneq >= L + 1;
+  uint32_t want[kPairWords], nwant = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kPairWords; w++) {
+    want[w] = order_kind ? uneq[w] : (inm[w] & ~uneq[w]);
+    nwant += __popc(want[w]);
+  }
+  uint32_t wb = 0, ub = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kPairWords; w++) {
+    const uint32_t p = lane + 32 * w;
+    const bool wanted = (want[w] >> lane) & 1u;
+    const uint32_t unw = inm[w] & ~want[w];
+    const uint32_t q = wanted ? wb + __popc(want[w] & lt) : nwant + ub + __popc(unw & lt);
+    wb += __popc(want[w]);
+    ub += __popc(unw);
+    if (p < P) {
+      T f = a[w], g = b[w];
+      if (order_kind && q < L) {
+        const bool bit = (v >> q) & 1u;
+        const T lo = a[w] < b[w] ? a[w] : b[w], hi = a[w] < b[w] ? b[w] : a[w];
+        f = bit ? hi : lo;
+        g = bit ? lo : hi;
+      } else if (!order_kind && q >= 1 && q <= L) {
+        g = (T)((v >> (q - 1)) & 1u);
+      }
+      A[mem(s + 2 * q)] = f;  // every pair was read above, before any write
+      A[mem(s + 2 * q + 1)] = g;
+    }
+  }
+}
+
+// Adds `off` to the value of the block at s (a later write: the kinds and
+// the pair order stay).
+template <typename T, typename Mem>
+__device__ __forceinline__ void warp_value_add(T* A, uint64_t s, uint32_t L, uint64_t off,
+                                               const Mem& mem) {
+  const uint32_t lane = threadIdx.x & 31u;
+  T a[2], b[2];
+#pragma unroll
+  for (uint32_t w = 0; w < 2; w++) {
+    const uint32_t p = lane + 32 * w;
+    if (p <= L) {
+      a[w] = ldcg(&A[mem(s + 2 * p)]);
+      b[w] = ldcg(&A[mem(s + 2 * p + 1)]);
+    }
+  }
+  const bool order_kind = __shfl_sync(0xffffffffu, a[0], 0) != __shfl_sync(0xffffffffu, b[0], 0);
+  uint64_t v = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < 2; w++) {
+    const uint32_t p = lane + 32 * w;
+    const bool bit = order_kind ? (p < L && a[w] > b[w]) : (p >= 1 && p <= L && b[w] != (T)0);
+    v |= (uint64_t)__ballot_sync(0xffffffffu, bit) << (32 * w);
+  }
+  if (!order_kind) v >>= 1;
+  const uint64_t nv = v + off;
+#pragma unroll
+  for (uint32_t w = 0; w < 2; w++) {
+    const uint32_t p = lane + 32 * w;
+    if (order_kind && p < L) {
+      const bool bit = (nv >> p) & 1u;
+      if (bit != (a[w] > b[w])) {
+        A[mem(s + 2 * p)] = b[w];
+        A[mem(s + 2 * p + 1)] = a[w];
+      }
+    } else if (!order_kind && p >= 1 && p <= L) {
+      const T g = (T)((nv >> (p - 1)) & 1u);
+      if (g != b[w]) A[mem(s + 2 * p + 1)] = g;
+    }
+  }
+}
+
+// Puts back the keys the overwrite kind replaced in the block at s.
+template <typename T, typename Mem>
+__device__ __forceinline__ void warp_value_restore(T* A, uint64_t s, uint32_t L, const Mem& mem) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const T a0 = ldcg(&A[mem(s)]), b0 = ldcg(&A[mem(s + 1)]);
+  if (a0 != b0) return;  // the order kind moved keys only
+#pragma unroll
+  for (uint32_t w = 0; w < 2; w++) {
+    const uint32_t p = lane + 32 * w;
+    if (p >= 1 && p <= L) A[mem(s + 2 * p + 1)] = ldcg(&A[mem(s + 2 * p)]);
+  }
+}
+
+template <typename T, bool KV, bool IMP>
 __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* vals, LowArgs a,
                                                        TaskScratch S) {
+  static_assert(!(IMP && KV), "values in key order: keys only");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ unsigned int flag;
   __shared__ unsigned long long red[kLT / 32];
@@ -277,64 +394,112 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
 
   stamp(2);
 
-  // ---- 3. block prefix v[i]
+  // ---- 3. block prefix: v[i] = predecessors in blocks 0..i (explicit), or
+  // the predecessors before block i kept in the order of its keys
   const uint64_t B = a.B;
   const uint64_t nb = n / B;
-  if (nb > a.nb_cap) {  // never expected: the host sizes the scratch for the array
-    if (tid == 0) atomicOr(S.status, kStatRing);
-    return;
-  }
-  if (nb > 0) {
-    // every CTA owns the blocks [b0, b1); its warps count one block each
-    // (16-byte loads) into v[b], the CTA turns those
-    // counts into an inclusive prefix over its range, then adds the totals of
-    // the CTAs before it
-    const uint64_t bpc = (nb + gridDim.x - 1) / gridDim.x;
-    const uint64_t b0 = min((uint64_t)blockIdx.x * bpc, nb), b1 = min(b0 + bpc, nb);
-    unsigned long long* V = reinterpret_cast<unsigned long long*>(a.v);
-    for (uint64_t b = b0 + warp; b < b1; b += kLT / 32) {
-      const uint64_t s = b * B, e = (b + 1 == nb) ? n : s + B;
-      const uint32_t c = flip ? count_span(A, n - e, n - s, lane, 32, isp)
-                              : count_span(A, s, e, lane, 32, isp);
-      unsigned long long cw = c;  // a block may hold more than 2^32 keys
+  const uint32_t Lb = 64u - (uint32_t)__clzll((long long)n);  // bits of a value in [0, n]
+  if constexpr (IMP) {
+    if (Lb > kMaxValueBits || B < 4ull * Lb + 2) {  // the host checks this first
+      if (tid == 0) atomicOr(S.status, kStatRing);
+      return;
+    }
+    if (nb > 0) {
+      // every CTA owns the blocks [b0, b1) and takes them kLT/32 at a time:
+      // each warp counts one block, then writes into it the count before it
+      // within the CTA's range; after the grid barrier the CTAs add the
+      // totals of the CTAs before them (a write of at most L pairs)
+      const uint64_t bpc = (nb + gridDim.x - 1) / gridDim.x;
+      const uint64_t b0 = min((uint64_t)blockIdx.x * bpc, nb), b1 = min(b0 + bpc, nb);
+      unsigned long long run = 0;
+      for (uint64_t base = b0; base < b1; base += kLT / 32) {
+        const uint64_t b = base + warp;
+        unsigned long long cw = 0;
+        if (b < b1) {
+          const uint64_t s0 = b * B, e = (b + 1 == nb) ? n : s0 + B;
+          cw = flip ? count_span(A, n - e, n - s0, lane, 32, isp)
+                    : count_span(A, s0, e, lane, 32, isp);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
-      if (lane == 0) __stcg(&V[b], cw);
+          for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
+        }
+        if (lane == 0) red[warp] = cw;
+        __syncthreads();
+        unsigned long long before = run, tot = 0;
+        for (uint32_t w = 0; w < kLT / 32; w++) {
+          const unsigned long long x = red[w];
+          tot += x;
+          if (w < warp) before += x;
+        }
+        if (b < b1) warp_value_first(A, b * B, Lb, before, mem);
+        run += tot;
+        __syncthreads();
+      }
+      if (tid == 0) __stcg(&a.cta[blockIdx.x], run);
+      if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
+      unsigned long long off = 0;
+      for (uint32_t c2 = tid; c2 < blockIdx.x; c2 += kLT) off += __ldcg(&a.cta[c2]);
+      off = cta_sum(off, red);
+      if (off != 0)
+        for (uint64_t b = b0 + warp; b < b1; b += kLT / 32) warp_value_add(A, b * B, Lb, off, mem);
+      if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
     }
-    __syncthreads();
-    // thread tid sums the counts [c0, c1) of its share of the range
-    const uint64_t per = (b1 - b0 + kLT - 1) / kLT;
-    const uint64_t c0 = min(b0 + tid * per, b1), c1 = min(c0 + per, b1);
-    unsigned long long own = 0;
-    for (uint64_t b = c0; b < c1; b++) own += __ldcg(&V[b]);
-    // exclusive scan of the shares across the CTA
-    unsigned long long incl = own;
+  } else {
+    if (nb > a.nb_cap) {  // never expected: the host sizes the scratch for the array
+      if (tid == 0) atomicOr(S.status, kStatRing);
+      return;
+    }
+    if (nb > 0) {
+      // every CTA owns the blocks [b0, b1); its warps count one block each
+      // (16-byte loads) into v[b], the CTA turns those counts into an
+      // inclusive prefix over its range, then adds the totals of the CTAs
+      // before it
+      const uint64_t bpc = (nb + gridDim.x - 1) / gridDim.x;
+      const uint64_t b0 = min((uint64_t)blockIdx.x * bpc, nb), b1 = min(b0 + bpc, nb);
+      unsigned long long* V = reinterpret_cast<unsigned long long*>(a.v);
+      for (uint64_t b = b0 + warp; b < b1; b += kLT / 32) {
+        const uint64_t s = b * B, e = (b + 1 == nb) ? n : s + B;
+        const uint32_t c = flip ? count_span(A, n - e, n - s, lane, 32, isp)
+                                : count_span(A, s, e, lane, 32, isp);
+        unsigned long long cw = c;  // a block may hold more than 2^32 keys
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long w = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= (uint32_t)o) incl += w;
+        for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
+        if (lane == 0) __stcg(&V[b], cw);
+      }
+      __syncthreads();
+      // thread tid sums the counts [c0, c1) of its share of the range
+      const uint64_t per = (b1 - b0 + kLT - 1) / kLT;
+      const uint64_t c0 = min(b0 + tid * per, b1), c1 = min(c0 + per, b1);
+      unsigned long long own = 0;
+      for (uint64_t b = c0; b < c1; b++) own += __ldcg(&V[b]);
+      // exclusive scan of the shares across the CTA
+      unsigned long long incl = own;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long w = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += w;
+      }
+      __syncthreads();
+      if (lane == 31) red[warp] = incl;
+      __syncthreads();
+      unsigned long long before = incl - own;
+      for (uint32_t w = 0; w < warp; w++) before += red[w];
+      unsigned long long ctatot = 0;
+      for (uint32_t w = 0; w < kLT / 32; w++) ctatot += red[w];
+      if (tid == 0) __stcg(&a.cta[blockIdx.x], ctatot);
+      if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
+      unsigned long long off = 0;
+      for (uint32_t c2 = tid; c2 < blockIdx.x; c2 += kLT) off += __ldcg(&a.cta[c2]);
+      off = cta_sum(off, red);
+      unsigned long long run = off + before;
+      for (uint64_t b = c0; b < c1; b++) {
+        run += __ldcg(&V[b]);
+        __stcg(&V[b], run);
+      }
+      if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
     }
-    __syncthreads();
-    if (lane == 31) red[warp] = incl;
-    __syncthreads();
-    unsigned long long before = incl - own;
-    for (uint32_t w = 0; w < warp; w++) before += red[w];
-    unsigned long long ctatot = 0;
-    for (uint32_t w = 0; w < kLT / 32; w++) ctatot += red[w];
-    if (tid == 0) __stcg(&a.cta[blockIdx.x], ctatot);
-    if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
-    unsigned long long off = 0;
-    for (uint32_t c2 = tid; c2 < blockIdx.x; c2 += kLT) off += __ldcg(&a.cta[c2]);
-    off = cta_sum(off, red);
-    unsigned long long run = off + before;
-    for (uint64_t b = c0; b < c1; b++) {
-      run += __ldcg(&V[b]);
-      __stcg(&V[b], run);
-    }
-    if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
   }
-
   stamp(3);
+  if (IMP && a.prefix_only) return;
 
   // ---- 4. Reorder: the prefix levels, innermost first
   if (tid == 0) {
@@ -356,6 +521,13 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   __syncthreads();
   const int L = nlev;
   const uint64_t mbase = mbase_s;
+  const uint64_t gwarp = ((uint64_t)blockIdx.x * kLT + tid) >> 5;
+  const uint64_t nwarps = gstride >> 5;
+  if constexpr (IMP) {
+    // the innermost prefix's blocks get their overwritten keys back first
+    for (uint64_t b = gwarp; b < mbase / B; b += nwarps) warp_value_restore(A, b * B, Lb, mem);
+    if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
+  }
   {
     // the innermost prefix, partitioned on chip: in memory it is [0, mbase)
     // or, for the reversed view, [n - mbase, n) with the roles back in place
@@ -373,8 +545,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   // keys (of this block or the warp's next one) load while this round's
   // targets do.
   constexpr uint32_t kRU = KV ? 4 : kUnroll;
-  const uint64_t gwarp = ((uint64_t)blockIdx.x * kLT + tid) >> 5;
-  const uint64_t nwarps = gstride >> 5;
+  static_assert(IMP ? 32 * kRU >= 2 * (kMaxValueBits + 1) : true, "a block's value in one round");
   const uint32_t lt = (1u << lane) - 1u;
   const unsigned long long* V = reinterpret_cast<const unsigned long long*>(a.v);
   for (int j = L - 1; j >= 0; j--) {
@@ -382,7 +553,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     uint64_t i = t0 + gwarp;
     if (i < NB) {
       uint64_t r0 = i * B, e = (i + 1 == NB) ? M : r0 + B;
-      uint64_t y = __ldcg(&V[i - 1]);
+      uint64_t y = IMP ? 0 : __ldcg(&V[i - 1]);  // kept in key order: read below
       T x[kRU];
 #pragma unroll
       for (uint32_t u = 0; u < kRU; u++) {
@@ -399,6 +570,43 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
           e1 = (i1 + 1 == NB) ? M : r1 + B;
         }
         const bool more = i1 < NB;
+        if constexpr (IMP) {
+          if (r0 == i * B) {  // the block's first round holds its value
+            // pair p is lanes 2p, 2p + 1 (mod 32) of round word p / 16
+            constexpr uint32_t kDecU = (kMaxValueBits + 1 + 15) / 16;
+            T nbv[kDecU];
+#pragma unroll
+            for (uint32_t u = 0; u < kDecU; u++) nbv[u] = __shfl_down_sync(0xffffffffu, x[u], 1);
+            const bool order_kind =
+                __shfl_sync(0xffffffffu, x[0], 0) != __shfl_sync(0xffffffffu, nbv[0], 0);
+            const bool even = (lane & 1u) == 0;
+            uint64_t val = 0;
+#pragma unroll
+            for (uint32_t u = 0; u < kDecU; u++) {
+              const uint32_t p = 16 * u + (lane >> 1);
+              const bool bit = even && (order_kind ? (p < Lb && x[u] > nbv[u])
+                                                   : (p >= 1 && p <= Lb && nbv[u] != (T)0));
+              const uint32_t bm = __ballot_sync(0xffffffffu, bit);
+              uint32_t c = 0;
+#pragma unroll
+              for (uint32_t j = 0; j < 16; j++) c |= ((bm >> (2 * j)) & 1u) << j;
+              val |= (uint64_t)c << (16 * u);
+            }
+            if (!order_kind) {
+              val >>= 1;
+#pragma unroll
+              for (uint32_t u = 0; u < kDecU; u++) {
+                const T ev = __shfl_up_sync(0xffffffffu, x[u], 1);
+                const uint32_t p = 16 * u + (lane >> 1);
+                if (!even && p >= 1 && p <= Lb) {
+                  x[u] = ev;
+                  A[mem(r0 + 32ull * u + lane)] = ev;
+                }
+              }
+            }
+            y = val;
+          }
+        }
         uint32_t f = 0;
 #pragma unroll
         for (uint32_t u = 0; u < kRU; u++)
@@ -429,7 +637,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
             const uint64_t q = r1 + 32ull * u + lane;
             if (q < e1) xn[u] = ldcg(&A[mem(q)]);
           }
-          if (next_block) yn = __ldcg(&V[i1 - 1]);
+          if (next_block) yn = IMP ? 0 : __ldcg(&V[i1 - 1]);
         }
 #pragma unroll
         for (uint32_t u = 0; u < kRU; u++) {
@@ -464,14 +672,17 @@ size_t lowspace_scratch_bytes(uint64_t n, uint64_t B, uint32_t grid) {
   return ((nb + 1) * 8 + 255) / 256 * 256 + ((size_t)grid * 8 + 255) / 256 * 256 + 256 + 256;
 }
 
-template <typename T, bool KV>
-cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, uint64_t n_cap,
-                            const LevelDesc* range_desc, T pivot, uint64_t B, uint64_t base_keys,
-                            void* var, const TaskScratch& S, uint64_t* split, LaunchCfg& cfg) {
+namespace {
+
+template <typename T, bool KV, bool IMP>
+cudaError_t launch_lowspace_impl(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi,
+                                 uint64_t n_cap, const LevelDesc* range_desc, T pivot, uint64_t B,
+                                 uint64_t base_keys, int prefix_only, void* var,
+                                 const TaskScratch& S, uint64_t* split, LaunchCfg& cfg) {
   cudaStream_t st = cfg.stream;
   // the scratch is laid out for the largest range it may see (the range may
-  // only be known on the device)
-  const uint64_t nb = B ? n_cap / B : 0;
+  // only be known on the device); values kept in key order need no counters
+  const uint64_t nb = (B && !IMP) ? n_cap / B : 0;
   unsigned char* p = static_cast<unsigned char*>(var);
   LowArgs a;
   a.lo = lo;
@@ -487,8 +698,9 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
   a.total = reinterpret_cast<unsigned long long*>(p);
   a.tl = reinterpret_cast<unsigned long long*>(p + 256);
   a.split = split;
+  a.prefix_only = prefix_only;
   const size_t smem = level_smem_bytes<T, KV>();
-  cudaError_t e = cudaFuncSetAttribute(lowspace_kernel<T, KV>,
+  cudaError_t e = cudaFuncSetAttribute(lowspace_kernel<T, KV, IMP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // a cooperative grid must fit on the device at once: size it by this kernel
@@ -496,7 +708,7 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lowspace_kernel<T, KV>, kLT,
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lowspace_kernel<T, KV, IMP>, kLT,
                                                          smem)) != cudaSuccess)
     return e;
   uint32_t grid = cfg.grid;
@@ -508,9 +720,37 @@ cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, u
   if (e == cudaSuccess) e = cudaMemsetAsync(a.tl, 0, 8 * kLowPhases, st);
   if (e != cudaSuccess) return e;
   if (cfg.phase_stamps) *cfg.phase_stamps = a.tl;
-  e = launch_cooperative(lowspace_kernel<T, KV>, grid, kLT, smem, st, keys, vals, a, S);
+  e = launch_cooperative(lowspace_kernel<T, KV, IMP>, grid, kLT, smem, st, keys, vals, a, S);
   cfg.launches++;
   return e;
+}
+
+}  // namespace
+
+template <typename T, bool KV>
+cudaError_t launch_lowspace(T* keys, uint64_t* vals, uint64_t lo, uint64_t hi, uint64_t n_cap,
+                            const LevelDesc* range_desc, T pivot, uint64_t B, uint64_t base_keys,
+                            void* var, const TaskScratch& S, uint64_t* split, LaunchCfg& cfg) {
+  return launch_lowspace_impl<T, KV, false>(keys, vals, lo, hi, n_cap, range_desc, pivot, B,
+                                            base_keys, 0, var, S, split, cfg);
+}
+
+size_t lowspace_implicit_scratch_bytes(uint32_t grid) { return lowspace_scratch_bytes(0, 1, grid); }
+
+uint32_t lowspace_value_bits(uint64_t n) {
+  uint32_t L = 0;
+  while (L < 64 && (n >> L) != 0) L++;
+  return L;
+}
+
+uint32_t lowspace_value_bits_max() { return kMaxValueBits; }
+
+template <typename T>
+cudaError_t launch_lowspace_implicit(T* keys, uint64_t n, T pivot, uint64_t B,
+                                     uint64_t base_keys, int prefix_only, void* var,
+                                     const TaskScratch& S, uint64_t* split, LaunchCfg& cfg) {
+  return launch_lowspace_impl<T, false, true>(keys, nullptr, 0, n, n, nullptr, pivot, B,
+                                              base_keys, prefix_only, var, S, split, cfg);
 }
 
 template cudaError_t launch_lowspace<uint64_t, false>(uint64_t*, uint64_t*, uint64_t, uint64_t,
@@ -525,5 +765,12 @@ template cudaError_t launch_lowspace<uint64_t, true>(uint64_t*, uint64_t*, uint6
                                                      uint64_t, const LevelDesc*, uint64_t, uint64_t,
                                                      uint64_t, void*, const TaskScratch&,
                                                      uint64_t*, LaunchCfg&);
+
+template cudaError_t launch_lowspace_implicit<uint64_t>(uint64_t*, uint64_t, uint64_t, uint64_t,
+                                                        uint64_t, int, void*, const TaskScratch&,
+                                                        uint64_t*, LaunchCfg&);
+template cudaError_t launch_lowspace_implicit<uint32_t>(uint32_t*, uint64_t, uint32_t, uint64_t,
+                                                        uint64_t, int, void*, const TaskScratch&,
+                                                        uint64_t*, LaunchCfg&);
 
 }  // namespace lp

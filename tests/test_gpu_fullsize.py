@@ -11,7 +11,8 @@ that hold at any size, computed on the device:
 
 Sizes: 2^30 uint64 at the 1%, 50% and 99% quantile pivots (8 GiB), 2^31
 uint32 (8 GiB), 2^29 key + payload pairs, the Strided / low-space / Hybrid
-variants at 2^30, and the 4096-instance batch (1.8 G keys).
+variants and the low-space form with values kept in key order at 2^30, and
+the 4096-instance batch (1.8 G keys).
 """
 import numpy as np
 import pytest
@@ -155,3 +156,16 @@ def test_batched_4096_instances(ctx):
             return k[order]
         assert torch.equal(seg_sorted(ki), seg_sorted(ko))
         s0 = s1
+
+
+@pytest.mark.parametrize("q", [50, 99])
+def test_implicit_u64_2pow30(ctx, q):
+    """The fully in-place form (block values kept in key order), 2^30 keys,
+    at the half and the 99% (role-swapped) pivots."""
+    n = 1 << 30
+    pivot = inputs.quantile_pivot(q, 100, 64)
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    lp.lp_fill_uniform_u64(keys, 0xC0FF6 + q)
+    inp = keys.clone()
+    t = lp.lp_lowspace_implicit_partition(ctx, keys, pivot)
+    check_props(inp, keys, t, pivot, 64)
