@@ -55,7 +55,8 @@ def parse():
                     help="default 30 (u64), 31 (u32), 29 (kv)")
     ap.add_argument("--dtype", choices=["u64", "u32", "kv"], default="u64")
     ap.add_argument("--quantile", type=int, default=50, help="percent of keys <= pivot")
-    ap.add_argument("--variant", choices=["smoothed", "strided", "lowspace", "hybrid"],
+    ap.add_argument("--variant", choices=["smoothed", "strided", "lowspace", "hybrid",
+                                          "implicit"],
                     default="smoothed")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
@@ -358,7 +359,10 @@ def run_ours(args):
     E = 16 if dt == "kv" else K          # bytes moved per key (key + payload)
     pivot = inputs.quantile_pivot(args.quantile, 100, 32 if dt == "u32" else 64)
     variant = {"smoothed": lp.LP_SMOOTHED, "strided": lp.LP_STRIDED,
-               "lowspace": lp.LP_LOWSPACE, "hybrid": lp.LP_HYBRID}[args.variant]
+               "lowspace": lp.LP_LOWSPACE, "hybrid": lp.LP_HYBRID,
+               "implicit": None}[args.variant]
+    if variant is None and dt == "kv":
+        raise SystemExit("--variant implicit: keys only")
     keys = torch.empty(n, dtype=torch.int32 if dt == "u32" else torch.int64, device="cuda")
     vals = torch.empty(n, dtype=torch.int64, device="cuda") if dt == "kv" else None
     d_split = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -372,7 +376,9 @@ def run_ours(args):
             lp.lp_fill_iota_u64(vals)
 
     def part(seed):
-        if dt == "u32":
+        if variant is None:  # values kept in key order: its own entry point, split to host
+            d_split.fill_(lp.lp_lowspace_implicit_partition(ctx, keys, pivot))
+        elif dt == "u32":
             lp.lp_partition_u32_async(ctx, keys, pivot, d_split, variant, seed=seed)
         elif dt == "kv":
             lp.lp_partition_kv_u64_async(ctx, keys, vals, pivot, d_split, variant, seed=seed)
@@ -429,11 +435,12 @@ def run_ours(args):
     k_ms = sum(kern_ms) / len(kern_ms)
     k_keys = sum(traffic_keys) / len(traffic_keys)
     kname = {"u64": "uint64_t", "u32": "uint32_t", "kv": "uint64_t, payload"}[dt]
-    if args.variant == "lowspace":
+    if args.variant in ("lowspace", "implicit"):
         # Sec. 5's accounting of the low-space partition: 3.5 read/write passes
         # and 0.5 read pass over the keys, i.e. 7.5 key bytes per key
         k_bytes = 7.5 * E * n
-        kernel = "lowspace_kernel<%s> (all phases, one cooperative launch)" % kname
+        kernel = "lowspace_kernel<%s%s> (all phases, one cooperative launch)" % (
+            kname, ", values in key order" if variant is None else "")
         traffic = None
     else:
         k_bytes = 2 * E * k_keys  # one read and one write of every key of every level
@@ -556,7 +563,10 @@ def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):
     for k in range(max(1, args.e2e_steps)):
         ev0.record(stream)
         keys.copy_(host_in, non_blocking=True)
-        lp.lp_partition_u64_async(ctx, keys, pivot, d_split, variant, seed=k)
+        if variant is None:
+            lp.lp_lowspace_implicit_partition(ctx, keys, pivot)
+        else:
+            lp.lp_partition_u64_async(ctx, keys, pivot, d_split, variant, seed=k)
         host_out.copy_(keys, non_blocking=True)
         host_split.copy_(d_split, non_blocking=True)
         ev1.record(stream)
@@ -565,7 +575,9 @@ def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):
     ms = sum(times) / len(times)
     return {"value": 3 * 8 * n / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + 8,
-            "path": "pinned host -> device, lp_partition_u64_async, device -> pinned host"}
+            "path": "pinned host -> device, %s, device -> pinned host" % (
+                "lp_lowspace_implicit_partition_u64" if variant is None
+                else "lp_partition_u64_async")}
 
 
 # ---------------------------------------------------------------- quicksort

@@ -273,7 +273,7 @@ lp_status implicit_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t B, uin
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   if (n == 0) { *split_out = 0; return LP_OK; }
   lp::LaunchCfg cfg{sizeof(T) == 8 ? c->grid_u64 : c->grid_u32, stream, 0, nullptr};
-  c->last_timed = false;
+  c->last_timed = c->timing;
   c->last_stream = stream;
   lp_status ls = ensure_var(c, lp::lowspace_implicit_scratch_bytes(cfg.grid), stream);
   if (ls != LP_OK) return ls;
@@ -282,9 +282,11 @@ lp_status implicit_impl(lp_ctx* c, T* keys, uint64_t n, T pivot, uint64_t B, uin
   cfg.phase_stamps = &c->last_low_tl;
   e = cudaMemsetAsync(S.status, 0, 4, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.bar, 0, 8, stream);
+  if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[0], stream);
   if (e == cudaSuccess)
     e = lp::launch_lowspace_implicit<T>(keys, n, pivot, B, base_keys ? base_keys : 1,
                                         prefix_only, c->d_var, S, S.split, cfg);
+  if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev[1], stream);
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return cuda_fail(c, e, "launch");
   return read_back(c, stream, split_out);
