@@ -405,42 +405,41 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
       return;
     }
     if (nb > 0) {
-      // every CTA owns the blocks [b0, b1) and takes them kLT/32 at a time:
-      // each warp counts one block, then writes into it the count before it
-      // within the CTA's range; after the grid barrier the CTAs add the
-      // totals of the CTAs before them (a write of at most L pairs)
+      // every CTA owns the blocks [b0, b1), every warp a contiguous run
+      // [w0, w1) of them: the warp counts each block and writes into it the
+      // count before it within the run; after one CTA barrier and one grid
+      // barrier it adds the totals of the runs and CTAs before (a write of at
+      // most L pairs per block)
       const uint64_t bpc = (nb + gridDim.x - 1) / gridDim.x;
       const uint64_t b0 = min((uint64_t)blockIdx.x * bpc, nb), b1 = min(b0 + bpc, nb);
+      const uint64_t bpw = (b1 - b0 + kLT / 32 - 1) / (kLT / 32);
+      const uint64_t w0 = min(b0 + warp * bpw, b1), w1 = min(w0 + bpw, b1);
       unsigned long long run = 0;
-      for (uint64_t base = b0; base < b1; base += kLT / 32) {
-        const uint64_t b = base + warp;
-        unsigned long long cw = 0;
-        if (b < b1) {
-          const uint64_t s0 = b * B, e = (b + 1 == nb) ? n : s0 + B;
-          cw = flip ? count_span(A, n - e, n - s0, lane, 32, isp)
-                    : count_span(A, s0, e, lane, 32, isp);
+      for (uint64_t b = w0; b < w1; b++) {
+        const uint64_t s0 = b * B, e = (b + 1 == nb) ? n : s0 + B;
+        unsigned long long cw = flip ? count_span(A, n - e, n - s0, lane, 32, isp)
+                                     : count_span(A, s0, e, lane, 32, isp);
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
-        }
-        if (lane == 0) red[warp] = cw;
-        __syncthreads();
-        unsigned long long before = run, tot = 0;
-        for (uint32_t w = 0; w < kLT / 32; w++) {
-          const unsigned long long x = red[w];
-          tot += x;
-          if (w < warp) before += x;
-        }
-        if (b < b1) warp_value_first(A, b * B, Lb, before, mem);
-        run += tot;
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, o);
+        warp_value_first(A, s0, Lb, run, mem);
+        run += cw;
       }
-      if (tid == 0) __stcg(&a.cta[blockIdx.x], run);
+      __syncthreads();
+      if (lane == 0) red[warp] = run;
+      __syncthreads();
+      unsigned long long before = 0, tot = 0;
+      for (uint32_t w = 0; w < kLT / 32; w++) {
+        const unsigned long long x = red[w];
+        tot += x;
+        if (w < warp) before += x;
+      }
+      if (tid == 0) __stcg(&a.cta[blockIdx.x], tot);
       if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
       unsigned long long off = 0;
       for (uint32_t c2 = tid; c2 < blockIdx.x; c2 += kLT) off += __ldcg(&a.cta[c2]);
-      off = cta_sum(off, red);
+      off = cta_sum(off, red) + before;
       if (off != 0)
-        for (uint64_t b = b0 + warp; b < b1; b += kLT / 32) warp_value_add(A, b * B, Lb, off, mem);
+        for (uint64_t b = w0; b < w1; b++) warp_value_add(A, b * B, Lb, off, mem);
       if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
     }
   } else {
