@@ -198,7 +198,7 @@ lp_status lp_ctx_set_batch_tuning(lp_ctx *ctx, const lp_batch_tuning *tuning);
  * Sorts keys[0..n) ascending in place: the quicksort of Sec. 5 ("A Full
  * Quicksort") built on the partition.  Level-synchronous: every level
  * partitions all open subarrays (more than 4096 keys) at once through the
- * batched engine, each by [x <= p] with p the median of three keys at
+ * batched engine, each by [x <= p] with p the median of 15 keys at
  * positions drawn from `seed` and the subarray's place; a subarray where no
  * key exceeds p is partitioned again by [x < p] and the keys equal to p are
  * final (the paper is silent on pivots and duplicates).  Subarrays of at most

@@ -33,13 +33,24 @@ __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
   if (q.eq) {
     d.pivot = q.pivot - 1;  // q.pivot > 0: a zero pivot never makes an equal-key item
   } else {
-    const T a = qs_ld(&keys[q.lo + range_of(sm_stream(h, 0), q.n)]);
-    const T b = qs_ld(&keys[q.lo + range_of(sm_stream(h, 1), q.n)]);
-    const T c = qs_ld(&keys[q.lo + range_of(sm_stream(h, 2), q.n)]);
-    const T mx = a > b ? a : b, mn = a > b ? b : a;
-    d.pivot = (uint64_t)(c > mx ? mx : (c < mn ? mn : c));
+    // the median of kQsSamples keys at seeded positions: all loads first,
+    // then an insertion sort in registers (fully unrolled)
+    T v[kQsSamples];
+#pragma unroll
+    for (uint32_t j = 0; j < kQsSamples; j++)
+      v[j] = qs_ld(&keys[q.lo + range_of(sm_stream(h, j), q.n)]);
+#pragma unroll
+    for (uint32_t j = 1; j < kQsSamples; j++) {
+#pragma unroll
+      for (uint32_t r = j; r > 0; r--) {
+        const T lo = v[r - 1] < v[r] ? v[r - 1] : v[r], hi = v[r - 1] < v[r] ? v[r] : v[r - 1];
+        v[r - 1] = lo;
+        v[r] = hi;
+      }
+    }
+    d.pivot = (uint64_t)v[kQsSamples / 2];
   }
-  d.salt = sm_stream(h, 3);  // the subarray and level name it, not its place in the list
+  d.salt = sm_stream(h, kQsSamples);  // the subarray and level name it, not its place in the list
   segs[J.seg_base + i] = d;
 }
 

@@ -5,7 +5,7 @@
 // and the subarrays of at most kQsCut keys are sorted by one CTA each in
 // shared memory (kernels in lp_qs.cuh).
 //
-// Per level: build the segment records (median-of-3 pivots), one batched
+// Per level: build the segment records (median-of-15 pivots), one batched
 // launch per slice of at most kSlice subarrays, split into children, sort the
 // level's small subarrays, read the next list's size back (one host
 // synchronisation per level).  Auxiliary memory: two item lists of at most
