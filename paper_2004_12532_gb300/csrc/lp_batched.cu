@@ -9,13 +9,17 @@
 //         (its unaligned head and tail are put in place, the split written);
 //         a residual range (after the first step) that one CTA's shared
 //         memory holds becomes a CTA task (the base case, finished on chip);
+//         one that kMcMinSlices or more CTAs (up to the grid) hold becomes a
+//         multi-CTA finish: that many CTAs stage a slice each, count, and
+//         after a grid barrier write a stable partition of the whole range;
 //         a first range of at most warp_cap keys gets a one-group step (g = 1:
 //         one warp partitions the whole range, as the paper's base case
 //         partitions serially); a larger one a step with g groups from the
 //         parameter rule.  Grid barrier; every CTA places its slice's tasks:
 //         CTA tasks and one-group segments in lists, multi-group segments
 //         with the prefix of their group counts.  Grid barrier.
-//   tasks every CTA takes CTA tasks from one counter; then every warp takes
+//   tasks the multi-CTA finishes run first, in windows of gridDim.x slices;
+//         every CTA takes CTA tasks from one counter; then every warp takes
 //         warp tasks from another -- the groups of multi-group segments first
 //         (binary search over their prefix), then the one-group segments --
 //         and partitions that group (warp_pair_group, as in the single
@@ -92,9 +96,10 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   using R = Tr<T, false>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ unsigned int flag;
-  __shared__ uint32_t wsum[4][R::Warps];
-  __shared__ uint32_t base_s[4];
-  __shared__ unsigned long long tot_s[4];
+  constexpr int KP = (int)kPlanKinds;
+  __shared__ uint32_t wsum[KP][R::Warps];
+  __shared__ uint32_t base_s[KP];
+  __shared__ unsigned long long tot_s[KP];
   __shared__ uint32_t fetch;
   __shared__ __align__(8) uint64_t cta_bar;  // the CTA tasks' bulk copies
   uint32_t cta_parity = 0;
@@ -116,11 +121,12 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   }
   __syncthreads();
 
-  // CTA-wide exclusive scan of (single, groups, multi, cta) over the slice
-  // in chunks of R::Threads; this thread's offsets and the chunk totals
-  auto cta_scan = [&](const uint32_t (&in)[4], uint32_t (&ex)[4], uint32_t (&tot)[4]) {
+  // CTA-wide exclusive scan of (single, groups, multi, cta, multi-CTA slices,
+  // multi-CTA segments) over the slice in chunks of R::Threads; this thread's
+  // offsets and the chunk totals
+  auto cta_scan = [&](const uint32_t (&in)[KP], uint32_t (&ex)[KP], uint32_t (&tot)[KP]) {
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
+    for (int c = 0; c < KP; c++) {
       uint32_t v = in[c];
 #pragma unroll
       for (uint32_t o = 1; o < 32; o <<= 1) {
@@ -132,7 +138,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
+    for (int c = 0; c < KP; c++) {
       uint32_t before = 0, all = 0;
       for (uint32_t w = 0; w < R::Warps; w++) {
         const uint32_t y = wsum[c][w];
@@ -150,10 +156,11 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
     unsigned long long* tr = round < kBatchRoundSlots ? B.tround + 4 * round : nullptr;
     if (stamp && tr) tr[0] = global_timer_ns();
     // ------------------------------------------------------------ plan A
-    uint32_t my[4] = {0, 0, 0, 0};  // singles, multi groups, multi segments, CTA tasks
+    // singles, multi groups, multi segments, CTA tasks, multi-CTA slices and segments
+    uint32_t my[KP] = {0, 0, 0, 0, 0, 0};
     for (uint32_t c0 = s_lo; c0 < s_hi; c0 += R::Threads) {
       const uint32_t s = c0 + tid;
-      uint32_t in[4] = {0, 0, 0, 0};
+      uint32_t in[KP] = {0, 0, 0, 0, 0, 0};
       if (s < s_hi) {
         SegDesc& d = segs[s];
         if (L2(d.state) == kSegOpen) {
@@ -183,14 +190,28 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
           } else {
             d.lo = lo;
             d.hi = hi;
-            atomicAdd(&B.totals[2], (unsigned long long)m);  // keys this round streams
             if (level > 0 && m <= cta_cap) {
               // a residual range one CTA holds: finished on chip (a CTA task);
               // first ranges that small stay one-warp steps, which many
               // small segments keep busy in parallel
+              atomicAdd(&B.totals[2], (unsigned long long)m);  // keys this round streams
               d.g = 0;
+              d.b = 1;
               in[3] = 1;
+            } else if (level > 0 && m >= (uint64_t)kMcMinSlices * cta_cap &&
+                       m <= (uint64_t)gridDim.x * cta_cap) {
+              // a residual range c CTAs hold (c >= kMcMinSlices: ranges that
+              // would take several more steps): finished on chip by c CTAs at
+              // once, a stable partition (the same as one CTA's); its keys
+              // are counted when it runs
+              const uint64_t c = (m + cta_cap - 1) / cta_cap;
+              d.g = 0;
+              d.b = c;
+              d.t = 0ull;  // slices done
+              in[4] = (uint32_t)c;
+              in[5] = 1;
             } else {
+              atomicAdd(&B.totals[2], (unsigned long long)m);  // keys this round streams
               StepParams P = choose_params(m, R::K, a.group_workers, a.line_bytes,
                                            level ? a.min_chunks_residual : a.min_chunks);
               if (m <= a.warp_cap || level + 1 >= a.max_rounds) P.g = 1;
@@ -206,28 +227,28 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
           }
         }
       }
-      uint32_t ex[4], tot[4];
+      uint32_t ex[KP], tot[KP];
       cta_scan(in, ex, tot);
 #pragma unroll
-      for (int c = 0; c < 4; c++) my[c] += tot[c];
+      for (int c = 0; c < KP; c++) my[c] += tot[c];
     }
-    if (tid < 4) B.cta_tot[4 * blockIdx.x + tid] = my[tid];
+    if (tid < KP) B.cta_tot[KP * blockIdx.x + tid] = my[tid];
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
 
     // ------------------------------------------------------------ plan B
     // this CTA's offsets: the totals of the CTAs before it; and the grand totals
     {
-      uint32_t before[4] = {0, 0, 0, 0}, all[4] = {0, 0, 0, 0};
+      uint32_t before[KP] = {0, 0, 0, 0, 0, 0}, all[KP] = {0, 0, 0, 0, 0, 0};
       for (uint32_t c = tid; c < gridDim.x; c += R::Threads) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const uint32_t y = __ldcg(&B.cta_tot[4 * c + q]);
+        for (int q = 0; q < KP; q++) {
+          const uint32_t y = __ldcg(&B.cta_tot[KP * c + q]);
           if (c < blockIdx.x) before[q] += y;
           all[q] += y;
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
+      for (int q = 0; q < KP; q++) {
 #pragma unroll
         for (uint32_t o = 16; o > 0; o >>= 1) {
           before[q] += __shfl_xor_sync(0xffffffffu, before[q], o);
@@ -236,34 +257,43 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
         if (lane == 0) wsum[q][warp] = before[q];
       }
       __syncthreads();
-      if (tid < 4) {
+      if (tid < KP) {
         uint32_t b = 0;
         for (uint32_t w = 0; w < R::Warps; w++) b += wsum[tid][w];
         base_s[tid] = b;
       }
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < 4; q++)
+      for (int q = 0; q < KP; q++)
         if (lane == 0) wsum[q][warp] = all[q];
       __syncthreads();
-      if (tid < 4) {
+      if (tid < KP) {
         unsigned long long t = 0;
         for (uint32_t w = 0; w < R::Warps; w++) t += wsum[tid][w];
         tot_s[tid] = t;
       }
       __syncthreads();
     }
-    uint32_t run[4] = {base_s[0], base_s[1], base_s[2], base_s[3]};
+    uint32_t run[KP];
+#pragma unroll
+    for (int c = 0; c < KP; c++) run[c] = base_s[c];
     for (uint32_t c0 = s_lo; c0 < s_hi; c0 += R::Threads) {
       const uint32_t s = c0 + tid;
-      uint32_t in[4] = {0, 0, 0, 0};
+      uint32_t in[KP] = {0, 0, 0, 0, 0, 0};
       if (s < s_hi && L2(segs[s].state) == kSegOpen) {
         const uint64_t g = L2(segs[s].g);
-        if (g == 0) in[3] = 1;
-        else if (g == 1) in[0] = 1;
-        else { in[1] = (uint32_t)g; in[2] = 1; }
+        if (g == 0) {
+          const uint64_t c = L2(segs[s].b);
+          if (c <= 1) in[3] = 1;
+          else { in[4] = (uint32_t)c; in[5] = 1; }
+        } else if (g == 1) {
+          in[0] = 1;
+        } else {
+          in[1] = (uint32_t)g;
+          in[2] = 1;
+        }
       }
-      uint32_t ex[4], tot[4];
+      uint32_t ex[KP], tot[KP];
       cta_scan(in, ex, tot);
       if (in[0]) B.singles[run[0] + ex[0]] = s;
       if (in[2]) {
@@ -271,30 +301,133 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
         B.mseg[run[2] + ex[2]] = s;
       }
       if (in[3]) B.ctalist[run[3] + ex[3]] = s;
+      if (in[5]) {
+        B.mcprefix[run[5] + ex[5]] = run[4] + ex[4];
+        B.mcseg[run[5] + ex[5]] = s;
+      }
 #pragma unroll
-      for (int c = 0; c < 4; c++) run[c] += tot[c];
+      for (int c = 0; c < KP; c++) run[c] += tot[c];
     }
     const unsigned long long n_single = tot_s[0], w_multi = tot_s[1];
     const uint32_t n_multi = (uint32_t)tot_s[2], n_cta = (uint32_t)tot_s[3];
+    const uint32_t n_mcslots = (uint32_t)tot_s[4], n_mc = (uint32_t)tot_s[5];
     if (blockIdx.x == 0 && tid == 0) {
       B.mprefix[n_multi] = w_multi;
+      B.mcprefix[n_mc] = n_mcslots;
       B.counters[0] = 0u;
       B.counters[1] = 0u;
       __threadfence();
     }
     if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
-    if (n_single == 0 && w_multi == 0 && n_cta == 0) break;  // every segment is done
+    if (n_single == 0 && w_multi == 0 && n_cta == 0 && n_mc == 0) break;  // all done
 
     // ------------------------------------------------------------ tasks
     const unsigned long long W = w_multi + n_single;
     if (stamp && tr) {
       tr[1] = global_timer_ns();
-      tr[3] = W + n_cta;
+      tr[3] = W + n_cta + n_mcslots;
     }
-    if (n_cta > 0) {  // CTA tasks first: they use the warps' shared memory
+    if (n_cta > 0 || n_mc > 0) {  // CTA tasks first: they use the warps' shared memory
       if (lane == 0)
         for (uint32_t st = 0; st < R::Stages; st++) mbar_inval(&ws.bar[st]);
       __syncthreads();
+      // multi-CTA finishes, in windows of gridDim.x slices: in a window
+      // starting at slice w0, CTA b stages and counts slice w0 + b if its
+      // finish [p, p + c) lies inside the window; after a grid barrier it
+      // writes its predecessors and successors to their final places, and
+      // the last slice of a finish to complete places the head and tail.  A
+      // finish cut by the window's end starts the next window.
+      for (uint32_t w0 = 0; w0 < n_mcslots;) {
+        auto finish_of = [&](uint32_t slot) {  // the last finish starting at or before slot
+          uint32_t lo_k = 0, hi_k = n_mc;
+          while (hi_k - lo_k > 1) {
+            const uint32_t mid = (lo_k + hi_k) >> 1;
+            if (__ldcg(&B.mcprefix[mid]) <= slot) lo_k = mid; else hi_k = mid;
+          }
+          return lo_k;
+        };
+        const uint32_t wend = w0 + gridDim.x;
+        const uint32_t slot = w0 + blockIdx.x;
+        uint32_t k = 0, p = 0, c = 0;
+        bool active = false;
+        if (slot < n_mcslots) {
+          k = finish_of(slot);
+          p = __ldcg(&B.mcprefix[k]);
+          c = __ldcg(&B.mcprefix[k + 1]) - p;
+          active = p >= w0 && (uint64_t)p + c <= wend;
+        }
+        uint32_t got = 0, s = 0;
+        uint64_t lo = 0, m = 0, a0 = 0, nj = 0;
+        if (active) {
+          s = __ldcg(&B.mcseg[k]);
+          SegDesc& d = segs[s];
+          lo = L2(d.lo);
+          m = L2(d.hi) - lo;
+          const uint64_t w = ((m + c - 1) / c + R::A - 1) / R::A * R::A;
+          a0 = min(m, (uint64_t)(slot - p) * w);
+          nj = min(m, a0 + w) - a0;
+          if (nj > 0)
+            got = cta_bulk_stage<T>(reinterpret_cast<T*>(d.keys) + lo + a0, (uint32_t)nj,
+                                    (T)L2(d.pivot), smem_raw, &cta_bar, cta_parity, S.status);
+          if (tid == 0) B.mccount[slot - w0] = got == ~0u ? 0u : got;
+        }
+        if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+        if (active && got != ~0u) {
+          // predecessors of the slices before this one, and of the whole range
+          unsigned long long before = 0, all = 0;
+          for (uint32_t q = tid; q < c; q += R::Threads) {
+            const uint32_t y = __ldcg(&B.mccount[p - w0 + q]);
+            all += y;
+            if (p + q < slot) before += y;
+          }
+#pragma unroll
+          for (uint32_t o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+          }
+          if (lane == 0) {
+            wsum[0][warp] = (uint32_t)before;
+            wsum[1][warp] = (uint32_t)all;
+          }
+          __syncthreads();
+          uint64_t pb = 0, pt = 0;
+          for (uint32_t w2 = 0; w2 < R::Warps; w2++) {
+            pb += wsum[0][w2];
+            pt += wsum[1][w2];
+          }
+          SegDesc& d = segs[s];
+          T* keys = reinterpret_cast<T*>(d.keys);
+          const T pivot = (T)L2(d.pivot);
+          if (nj > 0)
+            cta_bulk_scatter<T>(keys + lo + pb, keys + lo + pt + (a0 - pb), (uint32_t)nj, pivot,
+                                smem_raw);
+          __threadfence();
+          __syncthreads();
+          if (tid == 0) {
+            if (slot == p) atomicAdd(&B.totals[2], (unsigned long long)m);  // keys streamed
+            if (atomicAdd(&d.t, 1ull) + 1 == c) {  // the last slice: the others' writes are visible
+              __threadfence();
+              const unsigned long long t =
+                  seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), L2(d.body_count), pivot);
+              d.t = t;
+              a.splits[s] = t;
+              d.state = kSegDone;
+            }
+          }
+        }
+        __syncthreads();
+        // the next window: at the finish cut by this one's end, if any
+        uint32_t next = wend;
+        if (wend < n_mcslots) {
+          const uint32_t kc = finish_of(wend - 1);
+          const uint32_t pc = __ldcg(&B.mcprefix[kc]);
+          if (__ldcg(&B.mcprefix[kc + 1]) > wend) next = pc;
+        }
+        w0 = next;
+        // the next window's counts reuse B.mccount: every CTA has read this
+        // window's before any writes them again
+        if (w0 < n_mcslots && !grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+      }
       for (;;) {
         if (tid == 0) fetch = atomicAdd(&B.counters[1], 1u);
         __syncthreads();
@@ -417,7 +550,9 @@ size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t batch_scratch_bytes(uint32_t count) {
   return up256(((size_t)count + 1) * 8) + 3 * up256((size_t)count * 4) +
-         up256((size_t)kBatchMaxGrid * 4 * 4) + up256(kBatchRoundSlots * 4 * 8) + 256;
+         up256(((size_t)count + 1) * 4) + up256((size_t)count * 4) +
+         up256((size_t)kBatchMaxGrid * 4) + up256((size_t)kBatchMaxGrid * kPlanKinds * 4) +
+         up256(kBatchRoundSlots * 4 * 8) + 256;
 }
 
 BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint32_t* status) {
@@ -431,8 +566,14 @@ BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint
   p += up256((size_t)count * 4);
   B.ctalist = reinterpret_cast<uint32_t*>(p);
   p += up256((size_t)count * 4);
+  B.mcprefix = reinterpret_cast<uint32_t*>(p);
+  p += up256(((size_t)count + 1) * 4);
+  B.mcseg = reinterpret_cast<uint32_t*>(p);
+  p += up256((size_t)count * 4);
+  B.mccount = reinterpret_cast<uint32_t*>(p);
+  p += up256((size_t)kBatchMaxGrid * 4);
   B.cta_tot = reinterpret_cast<uint32_t*>(p);
-  p += up256((size_t)kBatchMaxGrid * 4 * 4);
+  p += up256((size_t)kBatchMaxGrid * kPlanKinds * 4);
   B.tround = reinterpret_cast<unsigned long long*>(p);
   p += up256(kBatchRoundSlots * 4 * 8);
   B.totals = reinterpret_cast<unsigned long long*>(p);

@@ -31,6 +31,11 @@ struct SegDesc {
 constexpr uint32_t kWarpCapBytes = 128u * 1024u;
 // CTAs of a batched launch, at most (plan space per CTA)
 constexpr uint32_t kBatchMaxGrid = 1024;
+// task kinds a plan counts per CTA
+constexpr uint32_t kPlanKinds = 6;
+// residual ranges of at least this many CTAs' shared memory (and at most the
+// grid's) are finished on chip by that many CTAs at once
+constexpr uint32_t kMcMinSlices = 16;
 // rounds recorded in BatchScratch::tround
 constexpr uint32_t kBatchRoundSlots = 12;
 
@@ -49,7 +54,11 @@ struct BatchScratch {
   uint32_t* mseg;               // multi-group segments: ids
   uint32_t* singles;            // one-group segments: ids
   uint32_t* ctalist;            // CTA-task segments: ids
-  uint32_t* cta_tot;            // per CTA: singles, groups, multi-group segments, CTA tasks
+  uint32_t* mcprefix;           // multi-CTA finishes: prefix of their CTA slices
+  uint32_t* mcseg;              // multi-CTA finishes: ids
+  uint32_t* mccount;            // per CTA slice: its predecessor count
+  uint32_t* cta_tot;            // per CTA: singles, groups, multi-group segments, CTA tasks,
+                                // multi-CTA slices, multi-CTA segments
   unsigned long long* totals;   // [2]: keys streamed
   unsigned long long* tround;   // per round: plan start, tasks start, tasks end (ns), tasks
   uint32_t* counters;           // task fetch counter

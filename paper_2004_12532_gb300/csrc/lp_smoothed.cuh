@@ -447,10 +447,14 @@ struct CtaBulk {
       Tr<T, false>::A;
 };
 
+// First half of a CTA's on-chip partition: stages keys[0..n) (16-byte
+// aligned, n <= CtaBulk<T>::Keys) in shared memory with one bulk copy and
+// ranks the predecessors by warp ballots in index order.  Returns their
+// count, or ~0u if the copy's wait gave up (status set).
 template <typename T>
-__device__ uint32_t cta_partition_bulk(T* __restrict__ keys, uint32_t n, T pivot,
-                                       unsigned char* smem, uint64_t* bar, uint32_t& parity,
-                                       uint32_t* status) {
+__device__ uint32_t cta_bulk_stage(const T* __restrict__ keys, uint32_t n, T pivot,
+                                   unsigned char* smem, uint64_t* bar, uint32_t& parity,
+                                   uint32_t* status) {
   constexpr uint32_t NT = Tr<T, false>::Threads, W = NT / 32;
   constexpr uint32_t FULL = 0xffffffffu;
   static_assert(((CtaBulk<T>::Keys + NT - 1) / NT) * W * 4 + 4 <= CtaBulk<T>::Head,
@@ -458,7 +462,6 @@ __device__ uint32_t cta_partition_bulk(T* __restrict__ keys, uint32_t n, T pivot
   uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
   T* sk = reinterpret_cast<T*>(smem + CtaBulk<T>::Head);
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
   const uint32_t bytes = n * (uint32_t)sizeof(T);
   if (tid == 0) {
     fence_proxy_async_smem();  // this shared memory was last written by threads
@@ -502,16 +505,46 @@ __device__ uint32_t cta_partition_bulk(T* __restrict__ keys, uint32_t n, T pivot
     if (lane == 0) cnt[(CtaBulk<T>::Head / 4) - 1] = run;
   }
   __syncthreads();
-  const uint32_t total = cnt[(CtaBulk<T>::Head / 4) - 1];
+  return cnt[(CtaBulk<T>::Head / 4) - 1];
+}
+
+// Second half: the staged keys' predecessors go to pred[0..) and their
+// successors to succ[0..), each in index order (stable).  Ends with a CTA
+// barrier (the shared memory may be reused at once).
+template <typename T>
+__device__ void cta_bulk_scatter(T* __restrict__ pred, T* __restrict__ succ, uint32_t n, T pivot,
+                                 const unsigned char* smem) {
+  constexpr uint32_t NT = Tr<T, false>::Threads, W = NT / 32;
+  constexpr uint32_t FULL = 0xffffffffu;
+  const uint32_t* cnt = reinterpret_cast<const uint32_t*>(smem);
+  const T* sk = reinterpret_cast<const T*>(smem + CtaBulk<T>::Head);
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t nch = (n + NT - 1) / NT;
   for (uint32_t c = 0; c < nch; c++) {
     const uint32_t q = c * NT + tid;
     const T x = q < n ? sk[q] : pivot;
     const bool f = q < n && x <= pivot;
     const uint32_t bal = __ballot_sync(FULL, f);
     const uint32_t pre = cnt[c * W + warp] + __popc(bal & lt);  // predecessors before q
-    if (q < n) keys[f ? pre : total + q - pre] = x;
+    if (q < n) {
+      if (f) pred[pre] = x;
+      else succ[q - pre] = x;
+    }
   }
   __syncthreads();
+}
+
+// The whole on-chip partition of keys[0..n) by one CTA.  Returns the
+// predecessor count, or ~0u if the copy's wait gave up (status set).  `bar`
+// is a CTA-wide mbarrier (count 1) and `parity` its phase.
+template <typename T>
+__device__ uint32_t cta_partition_bulk(T* __restrict__ keys, uint32_t n, T pivot,
+                                       unsigned char* smem, uint64_t* bar, uint32_t& parity,
+                                       uint32_t* status) {
+  const uint32_t total = cta_bulk_stage<T>(keys, n, pivot, smem, bar, parity, status);
+  if (total == ~0u) return ~0u;
+  cta_bulk_scatter<T>(keys, keys + total, n, pivot, smem);
   return total;
 }
 
