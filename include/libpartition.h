@@ -374,6 +374,31 @@ lp_status lp_lowspace_partition_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uin
                                     uint64_t B, uint64_t base_keys, cudaStream_t stream,
                                     uint64_t *split_out);
 
+/* ------------------------------------------------------------ host arrays
+ * Partitions keys[0..n), an array in HOST memory, in place: the same split t
+ * and postcondition as lp_partition_*.  The array travels to the device in
+ * chunks of about n/32 keys (at least 2^22), each partitioned there in place
+ * by the Smoothed Striding partition (Sec. 4) as soon as it arrives, while
+ * the predecessors and successors of the chunks already done are copied back
+ * to their final places: predecessors fill the host array from the front,
+ * successors from the back, and a host position is written only after its
+ * own chunk has reached the device.  Which end the next chunk comes from is
+ * decided by the counts of earlier chunks, so the result depends on the input
+ * and seed only.  Pinned host memory (cudaHostAlloc / cudaHostRegister) lets
+ * the copies in both directions and the partitions overlap; pageable memory
+ * works, serialised.  Device memory: a copy of the array (n keys), kept by
+ * ctx for later calls and freed by lp_ctx_destroy, plus the usual scratch.
+ * Ordered after earlier work on `stream`; returns when the host array holds
+ * the result (it synchronises).  *split_out (host) receives t.
+ * Errors: LP_ERR_INVALID_ARG for a null array with n > 0, a misaligned array
+ * or a null split_out; LP_ERR_OOM when the device copy cannot be allocated;
+ * LP_ERR_TIMEOUT / LP_ERR_CUDA as for lp_partition_*, after which the host
+ * array's content is unspecified. */
+lp_status lp_partition_host_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
+                                uint64_t seed, cudaStream_t stream, uint64_t *split_out);
+lp_status lp_partition_host_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t pivot,
+                                uint64_t seed, cudaStream_t stream, uint64_t *split_out);
+
 /* ------------------------- Blocked-Prefix-Sum partition, values in key order
  * The fully in-place form of Sec. 3 (An Implicit Parallel Prefix Sum; In-Place
  * Reordering; Lemma bitstore2, which allows repeated keys): the same phases as

@@ -111,6 +111,8 @@ _SIGS = {
     "lp_partition_u64_noalloc": (_i, [_p, _u64, _u64, _i, _u64, _p, _p]),
     "lp_lowspace_partition_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _p, _pu64]),
     "lp_lowspace_partition_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _p, _pu64]),
+    "lp_partition_host_u64": (_i, [_p, _p, _u64, _u64, _u64, _p, _pu64]),
+    "lp_partition_host_u32": (_i, [_p, _p, _u64, _u32, _u64, _p, _pu64]),
     "lp_lowspace_implicit_partition_u64": (_i, [_p, _p, _u64, _u64, _u64, _u64, _p, _pu64]),
     "lp_lowspace_implicit_partition_u32": (_i, [_p, _p, _u64, _u32, _u64, _u64, _p, _pu64]),
     "lp_lowspace_implicit_prefix_u64": (_i, [_p, _p, _u64, _u64, _u64, _p, _pu64]),
@@ -433,6 +435,24 @@ def lp_lowspace_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):
     f = lib().lp_lowspace_partition_u64 if bits == 64 else lib().lp_lowspace_partition_u32
     t = C.c_uint64()
     ctx.check(f(ctx.h, p, n, int(pivot), int(B), int(base_keys), _stream(stream), C.byref(t)))
+    return int(t.value)
+
+
+def lp_partition_host(ctx, keys, pivot, seed=0, stream=None):
+    """Partition a CPU tensor (int64 / int32 holding uint64 / uint32 keys) in
+    place through lp_partition_host_*; pinned memory lets the copies overlap.
+    Returns the split t."""
+    if not isinstance(keys, torch.Tensor) or keys.is_cuda:
+        raise TypeError("expected a CPU tensor")
+    if not keys.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    bits = keys.element_size() * 8
+    if bits not in (32, 64):
+        raise TypeError("expected 32- or 64-bit keys")
+    f = lib().lp_partition_host_u64 if bits == 64 else lib().lp_partition_host_u32
+    t = C.c_uint64()
+    ctx.check(f(ctx.h, C.c_void_p(keys.data_ptr()), keys.numel(), int(pivot), int(seed),
+                _stream(stream), C.byref(t)))
     return int(t.value)
 
 

@@ -337,6 +337,7 @@ lp_status lp_ctx_destroy(lp_ctx* c) {
   if (c->d_batch) cudaFree(c->d_batch);
   if (c->h_batch) cudaFreeHost(c->h_batch);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  lp::hostpart_free(c);
   delete c;
   return LP_OK;
 }

@@ -38,7 +38,12 @@ struct lp_ctx {
   unsigned long long* last_batch_tround = nullptr;   // its round timestamps
   lp_sort_stats sort_stats{};                         // of the last quicksort
   unsigned long long* last_low_tl = nullptr;          // phase stamps of the last LP_LOWSPACE call
+  void* hostpart = nullptr;  // state of the host-array partition (lp_hostpart.cu)
 };
+
+namespace lp {
+void hostpart_free(lp_ctx* c);
+}
 
 
 lp_status lp_fail(lp_ctx* c, lp_status s, const char* what);
