@@ -13,9 +13,11 @@ roofline: the dominant kernel is the level-0 Partial Partition Step; its
           algorithmic traffic is one read and one write of every key in its
           range (2 * 8 * n bytes), timed live with the library's per-level
           CUDA events, against the measured HBM copy bandwidth.
-e2e     = the same metric through the C ABI with host buffers: pinned host ->
-          device copy of the keys, partition, device -> host copy of the
-          partitioned keys and the split, all inside the timed region.
+e2e     = the same metric through the C ABI with a host buffer:
+          lp_partition_host_u64 partitions a pinned host array in place
+          (chunked uploads, device partitions and copies back, overlapping),
+          all inside the timed region.  (--workload quicksort / batched: a
+          pinned host -> device copy, the device call, a device -> host copy.)
 cpu_baseline: the serial CPU oracle (two-pointer partition) on a bounded
           sample of the same workload, on one host core.
 
