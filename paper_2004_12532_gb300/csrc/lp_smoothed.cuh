@@ -278,35 +278,80 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     const uint32_t m = min(SL, PR);
     if (m > 0) {
       const uint32_t exl = (incl - own) & 0xffffu, exr = (incl - own) >> 16;
-      uint32_t rl[NB], rr[NB];
+      if constexpr (NB > 8) {
+        // 16 slots per lane (4-byte keys, issue-bound): ranks by running
+        // counts; the slots that move form a prefix of each lane's
+        // successors of L (predecessors of R) in slot order
+        uint32_t cl = exl, cr = exr, ml = 0, mr = 0;
 #pragma unroll
-      for (uint32_t j = 0; j < NB; j++) {
-        const uint32_t u = j / V, v = j % V;
-        const uint32_t below = (1u << j) - 1u;
-        rl[j] = ((lsucc >> j) & 1u) ? exl + __popc(lsucc & below) : 0xffffffffu;
-        rr[j] = ((rpred >> j) & 1u) ? exr + __popc(rpred & below) : 0xffffffffu;
-        if (rl[j] < m) {
-          sm.xbuf[0][rl[j]] = Lr.x[u][v];
-          if constexpr (KV) sm.vxbuf[0][rl[j]] = Lr.y[u][v];
+        for (uint32_t j = 0; j < NB; j++) {
+          const uint32_t u = j / V, v = j % V;
+          const uint32_t bl = (lsucc >> j) & 1u, br = (rpred >> j) & 1u;
+          if (bl && cl < m) {
+            sm.xbuf[0][cl] = Lr.x[u][v];
+            if constexpr (KV) sm.vxbuf[0][cl] = Lr.y[u][v];
+            ml |= 1u << j;
+          }
+          if (br && cr < m) {
+            sm.xbuf[1][cr] = Rr.x[u][v];
+            if constexpr (KV) sm.vxbuf[1][cr] = Rr.y[u][v];
+            mr |= 1u << j;
+          }
+          cl += bl;
+          cr += br;
         }
-        if (rr[j] < m) {
-          sm.xbuf[1][rr[j]] = Rr.x[u][v];
-          if constexpr (KV) sm.vxbuf[1][rr[j]] = Rr.y[u][v];
-        }
-      }
-      __syncwarp();
+        __syncwarp();
+        cl = exl;
+        cr = exr;
 #pragma unroll
-      for (uint32_t j = 0; j < NB; j++) {
-        const uint32_t u = j / V, v = j % V;
-        if (rl[j] < m) {
-          Lr.x[u][v] = sm.xbuf[1][rl[j]];
-          if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][rl[j]];
-          Lr.pred |= 1u << j;
+        for (uint32_t j = 0; j < NB; j++) {
+          const uint32_t u = j / V, v = j % V;
+          const uint32_t bl = (ml >> j) & 1u, br = (mr >> j) & 1u;
+          if (bl) {
+            Lr.x[u][v] = sm.xbuf[1][cl];
+            if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][cl];
+          }
+          if (br) {
+            Rr.x[u][v] = sm.xbuf[0][cr];
+            if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][cr];
+          }
+          cl += bl;
+          cr += br;
         }
-        if (rr[j] < m) {
-          Rr.x[u][v] = sm.xbuf[0][rr[j]];
-          if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][rr[j]];
-          Rr.pred &= ~(1u << j);
+        Lr.pred |= ml;
+        Rr.pred &= ~mr;
+      } else {
+        // 8 slots per lane: each slot's rank from a population count
+        uint32_t rl[NB], rr[NB];
+#pragma unroll
+        for (uint32_t j = 0; j < NB; j++) {
+          const uint32_t u = j / V, v = j % V;
+          const uint32_t below = (1u << j) - 1u;
+          rl[j] = ((lsucc >> j) & 1u) ? exl + __popc(lsucc & below) : 0xffffffffu;
+          rr[j] = ((rpred >> j) & 1u) ? exr + __popc(rpred & below) : 0xffffffffu;
+          if (rl[j] < m) {
+            sm.xbuf[0][rl[j]] = Lr.x[u][v];
+            if constexpr (KV) sm.vxbuf[0][rl[j]] = Lr.y[u][v];
+          }
+          if (rr[j] < m) {
+            sm.xbuf[1][rr[j]] = Rr.x[u][v];
+            if constexpr (KV) sm.vxbuf[1][rr[j]] = Rr.y[u][v];
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (uint32_t j = 0; j < NB; j++) {
+          const uint32_t u = j / V, v = j % V;
+          if (rl[j] < m) {
+            Lr.x[u][v] = sm.xbuf[1][rl[j]];
+            if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][rl[j]];
+            Lr.pred |= 1u << j;
+          }
+          if (rr[j] < m) {
+            Rr.x[u][v] = sm.xbuf[0][rr[j]];
+            if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][rr[j]];
+            Rr.pred &= ~(1u << j);
+          }
         }
       }
       __syncwarp();  // the buffer is free for the next swap
