@@ -181,3 +181,34 @@ def test_residual_tuning_keeps_results_valid(ctx, mcr):
         check_batch(to_host(buf, np.uint64), host, offs, sizes, pivots, splits.cpu().numpy())
     finally:
         lp.lp_ctx_set_batch_tuning(ctx)
+
+
+def test_multi_cta_finish_same_in_any_batch(ctx):
+    """Segments large enough that their first step leaves open ranges of 16
+    or more CTAs' shared memory, which several CTAs finish on chip at once,
+    and enough of them that the slices take several windows of the grid: each
+    result equals the oracle's, and is byte for byte the result of the same
+    segment at the same place in a batch of its own."""
+    sizes = [(1 << 24) + 3] * 3 + [(1 << 23) + 1001] * 4 + [5000, 70001]
+    host, offs, pivots = make_batch(sizes, 99)
+    buf = to_dev(host)
+    views = [buf[o:o + n] for o, n in zip(offs, sizes)]
+    splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+    lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=6)
+    torch.cuda.synchronize()
+    out = to_host(buf, np.uint64)
+    check_batch(out, host, offs, sizes, pivots, splits.cpu().numpy())
+    for s in (0, 4):
+        o, n = offs[s], sizes[s]
+        # the same offset modulo 16 bytes as in the batch buffer, so the
+        # same unaligned head and body
+        k = o % 2
+        whole = to_dev(host[o - k:o + n])
+        alone = whole[k:]
+        empty = whole[0:0]
+        sp = torch.zeros(s + 1, dtype=torch.int64, device="cuda")
+        lp.lp_partition_batched_u64(ctx, [empty] * s + [alone], [0] * s + [pivots[s]], sp,
+                                    seed=6)
+        torch.cuda.synchronize()
+        assert int(sp[s].item()) == int(splits[s].item())
+        assert np.array_equal(to_host(alone, np.uint64), out[o:o + n])
