@@ -233,7 +233,11 @@ def run_reference(args):
     if args.workload == "serve":
         return run_reference_serve(args)
     import oracle
-    pivot = inputs.quantile_pivot(1, 2)
+    if args.dtype != "u64":
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the reference arm times uint64 partitions only"}))
+        return
+    pivot = inputs.quantile_pivot(args.quantile, 100, 64)
     log2s = min(args.log2n, 26)
     n = 1 << log2s
     for w in range(args.warmup):
@@ -253,8 +257,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "partition u64 n=2^%d pivot=2^63-1 (50%%)" % args.log2n,
-                   "oracle": "serial two-pointer partition (CPU)"},
+        "config": {"workload": "partition u64 n=2^%d pivot at %d%% quantile, %s" % (
+                       args.log2n, args.quantile, args.variant),
+                   "n": 1 << args.log2n, "pivot": pivot, "variant": args.variant,
+                   "dtype": "u64", "oracle": "serial two-pointer partition (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -295,6 +301,7 @@ def run_reference_sort(args):
 
 def run_reference_batched(args):
     sizes, _, _ = batch_layout(args.instances, args.seed)
+    keys_total = int(sum(int(m) for m in sizes))
     for w in range(args.warmup):
         cpu_oracle_batch(sizes[:8], args.seed + w, 0.5)
     vals = []
@@ -307,7 +314,8 @@ def run_reference_batched(args):
     ms = keys / args.steps / (v * 1e9) * 1e3
     reference_line(args, "batched partition keys/s (%d uint64 instances, sizes log-uniform "
                    "[2^8, 2^22])" % args.instances, v, "Gkeys/s", ms,
-                   "batched partition, %d instances" % args.instances,
+                   "batched partition, %d instances, %d keys in all" % (args.instances,
+                                                                         keys_total),
                    "serial two-pointer partition per instance (CPU)",
                    "about 2 s of instances per step, in batch order")
 
@@ -341,7 +349,8 @@ def run_reference_serve(args):
     reference_line(args, "served keys/s (Poisson %.0f req/s, 70%% partition / 30%% sort, sizes "
                    "log-uniform [2^10, 2^26], uint32/uint64)" % args.rate, v, "Gkeys/s",
                    keys_all / args.steps / (v * 1e9) * 1e3,
-                   "serve, requests one at a time", "serial partition / quicksort per request",
+                   "serve %d requests per step at %.0f req/s" % (args.requests, args.rate),
+                   "serial partition / quicksort per request, one at a time",
                    "requests in stream order until 1 s of service time is spent (one large "
                    "sort can overrun it), service time only", dtype="u32+u64")
 
