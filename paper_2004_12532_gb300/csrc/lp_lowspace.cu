@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   // already).  Blocks and their targets are disjoint, so the next round's
   // keys (of this block or the warp's next one) load while this round's
   // targets do.
-  constexpr uint32_t kRU = KV ? 4 : kUnroll;
+  constexpr uint32_t kRU = KV ? 4 : (sizeof(T) == 4 ? 2 * kUnroll : kUnroll);
   static_assert(IMP ? 32 * kRU >= 2 * (kMaxValueBits + 1) : true, "a block's value in one round");
   const uint32_t lt = (1u << lane) - 1u;
   const unsigned long long* V = reinterpret_cast<const unsigned long long*>(a.v);
