@@ -151,6 +151,12 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
     __syncthreads();
   };
 
+  // grid barrier; false (status set) if this CTA gave up waiting
+  auto sync_grid = [&]() -> bool {
+    if (grid_barrier(S.bar, gridDim.x, &flag)) return true;
+    if (tid == 0) atomicOr(S.status, kStatTimeout);
+    return false;
+  };
   const bool stamp = blockIdx.x == 0 && tid == 0;
   for (uint32_t round = 0; round <= a.max_rounds; round++) {
     unsigned long long* tr = round < kBatchRoundSlots ? B.tround + 4 * round : nullptr;
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
       for (int c = 0; c < KP; c++) my[c] += tot[c];
     }
     if (tid < KP) B.cta_tot[KP * blockIdx.x + tid] = my[tid];
-    if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+    if (!sync_grid()) return;
 
     // ------------------------------------------------------------ plan B
     // this CTA's offsets: the totals of the CTAs before it; and the grand totals
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
       B.counters[1] = 0u;
       __threadfence();
     }
-    if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+    if (!sync_grid()) return;
     if (n_single == 0 && w_multi == 0 && n_cta == 0 && n_mc == 0) break;  // all done
 
     // ------------------------------------------------------------ tasks
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
                                     (T)L2(d.pivot), smem_raw, &cta_bar, cta_parity, S.status);
           if (tid == 0) B.mccount[slot - w0] = got == ~0u ? 0u : got;
         }
-        if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+        if (!sync_grid()) return;
         if (active && got != ~0u) {
           // predecessors of the slices before this one, and of the whole range
           unsigned long long before = 0, all = 0;
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
         w0 = next;
         // the next window's counts reuse B.mccount: every CTA has read this
         // window's before any writes them again
-        if (w0 < n_mcslots && !grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+        if (w0 < n_mcslots && !sync_grid()) return;
       }
       for (;;) {
         if (tid == 0) fetch = atomicAdd(&B.counters[1], 1u);
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
       }
     }
     __syncwarp();
-    if (!grid_barrier(S.bar, gridDim.x, &flag)) { if (tid == 0) atomicOr(S.status, kStatTimeout); return; }
+    if (!sync_grid()) return;
     if (stamp && tr) tr[2] = global_timer_ns();
   }
   __syncthreads();

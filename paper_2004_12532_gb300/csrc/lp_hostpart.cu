@@ -149,6 +149,14 @@ lp_status host_partition(lp_ctx* c, T* host, uint64_t n, T pivot, uint64_t seed,
       (e = cudaStreamWaitEvent(H.s_comp, H.ev_start, 0)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(H.s_down, H.ev_start, 0)) != cudaSuccess)
     return lp_cuda_fail(c, e, "order after the caller's stream");
+  // an error after copies were queued: let them finish before returning, so
+  // nothing writes the caller's host array after the call
+  auto bail = [&](lp_status st) {
+    cudaStreamSynchronize(H.s_up);
+    cudaStreamSynchronize(H.s_comp);
+    cudaStreamSynchronize(H.s_down);
+    return st;
+  };
   T* dev = static_cast<T*>(H.d_buf);
   TaskScratch S = c->task;
   LaunchCfg cfg{sizeof(T) == 8 ? c->grid_u64 : c->grid_u32, H.s_comp, 0, nullptr};
@@ -166,36 +174,37 @@ lp_status host_partition(lp_ctx* c, T* host, uint64_t n, T pivot, uint64_t seed,
                                H.s_up)) != cudaSuccess ||
           (e = cudaEventRecord(H.ev_up[j], H.s_up)) != cudaSuccess ||
           (e = cudaStreamWaitEvent(H.s_comp, H.ev_up[j], 0)) != cudaSuccess)
-        return lp_cuda_fail(c, e, "upload");
+        return bail(lp_cuda_fail(c, e, "upload"));
       if ((e = launch_smoothed<T, false>(dev + b, nullptr, len, pivot, seed + k, 0, S, cfg)) !=
           cudaSuccess)
-        return lp_cuda_fail(c, e, "partition of a chunk");
+        return bail(lp_cuda_fail(c, e, "partition of a chunk"));
       if ((e = cudaMemcpyAsync(H.h_slots + 2 * j, S.split, 8, cudaMemcpyDeviceToHost,
                                H.s_comp)) != cudaSuccess ||
           (e = cudaMemcpyAsync(H.h_slots + 2 * j + 1, S.status, 4, cudaMemcpyDeviceToHost,
                                H.s_comp)) != cudaSuccess ||
           (e = cudaEventRecord(H.ev_part[j], H.s_comp)) != cudaSuccess)
-        return lp_cuda_fail(c, e, "read a chunk's split");
+        return bail(lp_cuda_fail(c, e, "read a chunk's split"));
     }
     const uint32_t j = plan.processed();
-    if (j >= plan.uploads()) return lp_fail(c, LP_ERR_INTERNAL, "host partition plan stalled");
+    if (j >= plan.uploads())
+      return bail(lp_fail(c, LP_ERR_INTERNAL, "host partition plan stalled"));
     if ((e = cudaEventSynchronize(H.ev_part[j])) != cudaSuccess)
-      return lp_cuda_fail(c, e, "partition of a chunk");
+      return bail(lp_cuda_fail(c, e, "partition of a chunk"));
     status |= (uint32_t)(H.h_slots[2 * j + 1] & 0xffffffffu);
     plan.partitioned(H.h_slots[2 * j]);
     pieces.clear();
     plan.take_pieces(pieces);
     if (!pieces.empty() && (e = cudaStreamWaitEvent(H.s_down, H.ev_part[j], 0)) != cudaSuccess)
-      return lp_cuda_fail(c, e, "order the copies back");
+      return bail(lp_cuda_fail(c, e, "order the copies back"));
     for (const HostPiece& p : pieces)
       if ((e = cudaMemcpyAsync(host + p.host, dev + p.dev, p.len * sizeof(T),
                                cudaMemcpyDeviceToHost, H.s_down)) != cudaSuccess)
-        return lp_cuda_fail(c, e, "copy back");
+        return bail(lp_cuda_fail(c, e, "copy back"));
   }
   if ((e = cudaEventRecord(H.ev_end, H.s_down)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(stream, H.ev_end, 0)) != cudaSuccess ||
       (e = cudaEventSynchronize(H.ev_end)) != cudaSuccess)
-    return lp_cuda_fail(c, e, "finish the copies back");
+    return bail(lp_cuda_fail(c, e, "finish the copies back"));
   c->last_launches = cfg.launches;
   *split_out = plan.split();
   if (status & kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out");
