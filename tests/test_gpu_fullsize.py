@@ -68,9 +68,10 @@ def test_u64_2pow30(ctx, q):
 
 
 @pytest.mark.parametrize("variant", [lp.LP_STRIDED, lp.LP_LOWSPACE, lp.LP_HYBRID])
-def test_variants_u64_2pow30(ctx, variant):
+@pytest.mark.parametrize("q", [(1, 2), (99, 100)])
+def test_variants_u64_2pow30(ctx, variant, q):
     n = 1 << 30
-    pivot = inputs.quantile_pivot(1, 2, 64)
+    pivot = inputs.quantile_pivot(q[0], q[1], 64)
     keys = torch.empty(n, dtype=torch.int64, device="cuda")
     lp.lp_fill_uniform_u64(keys, 0xC0FF3 + variant)
     inp = keys.clone()
@@ -169,3 +170,18 @@ def test_implicit_u64_2pow30(ctx, q):
     inp = keys.clone()
     t = lp.lp_lowspace_implicit_partition(ctx, keys, pivot)
     check_props(inp, keys, t, pivot, 64)
+
+
+def test_host_array_u64_2pow30(ctx):
+    """The host-array entry point at the full size: a pinned 8 GiB array,
+    partitioned in place through lp_partition_host_u64, checked on the
+    device."""
+    n = 1 << 30
+    pivot = inputs.quantile_pivot(1, 2, 64)
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    lp.lp_fill_uniform_u64(keys, 0xC0FF7)
+    host = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    host.copy_(keys)
+    t = lp.lp_partition_host(ctx, host, pivot, seed=1)
+    out = host.to("cuda")
+    check_props(keys, out, t, pivot, 64)
