@@ -24,6 +24,15 @@ namespace lp {
 
 size_t level_desc_bytes() { return sizeof(LevelDesc); }
 
+namespace {
+// groups per warp at level 0 of the recursive partition, at most (measured:
+// 8 for keys, 16 for key + payload pairs at 2^30 keys on GB300)
+template <bool KV>
+constexpr uint64_t kLevel0GroupsPerWarp = KV ? 16 : 8;
+// ... and chunks per group, at least (shorter groups cost more than they save)
+constexpr uint32_t kLevel0MinChunks = 128;
+}  // namespace
+
 // ------------------------------------------------------------ scratch layout
 size_t task_scratch_bytes(uint32_t grid) {
   return sizeof(LevelDesc) * kMaxLevels + 64 /* status */ + 64 /* barrier, t_end */ +
@@ -41,6 +50,8 @@ TaskScratch carve_scratch(void* base, uint32_t grid) {
   p += 64;
   S.bar = reinterpret_cast<uint32_t*>(p);
   S.t_end = reinterpret_cast<unsigned long long*>(p + 8);
+  static_assert(16 + 4 * kMaxLevels <= 64, "the group counters share the barrier's 64 bytes");
+  S.fetch = reinterpret_cast<uint32_t*>(p + 16);
   p += 64;
   S.counts = reinterpret_cast<uint32_t*>(p);
   return S;
@@ -54,6 +65,7 @@ __global__ void desc_init_kernel(TaskScratch S) {
     d.vmax = 0ull;
     d.count = 0ull;
     d.lo = d.hi = d.b = d.g = d.t_start = 0ull;
+    S.fetch[t] = 0u;
   }
   if (t == 0) {
     *S.status = 0u;
@@ -141,14 +153,27 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
     }
 
     // a Partial Partition Step (parameter rule of lp_plan.h); the last level,
-    // should a range still be open, is one group
-    const StepParams P = choose_params(n, R::K, total_warps, R::LineBytes);
+    // should a range still be open, is one group.  Warps take groups one at a
+    // time from a counter, so that they finish together.  Level 0 of the
+    // recursion has up to kLevel0GroupsPerWarp groups per warp (the tail of a
+    // level costs more than the wider open range more groups leave); later
+    // levels, and a single step whose open range another algorithm cleans
+    // up, one per warp (longer groups leave a narrower open range)
+    const bool wide = L == 0 && a.max_levels > 1;
+    const uint64_t workers = wide ? total_warps * kLevel0GroupsPerWarp<KV> : total_warps;
+    const StepParams P =
+        wide ? choose_params(n, R::K, workers, R::LineBytes, kLevel0MinChunks)
+             : choose_params(n, R::K, workers, R::LineBytes);
     const uint64_t b = P.b;
     const uint64_t g = (L == kMaxLevels - 1) ? 1 : P.g;
     if (leader) { S.desc[L].b = b; S.desc[L].g = g; }
     const StepGeom G = make_geom(n, b, g, level_seed(a.seed, (uint64_t)L),
                                  (a.strided && L == 0) ? 1 : 0);
-    for (uint64_t i = (uint64_t)blockIdx.x * R::Warps + warp; i < G.g; i += total_warps) {
+    for (;;) {
+      uint32_t i = 0;
+      if (lane == 0) i = atomicAdd(&S.fetch[L], 1u);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if (i >= G.g) break;
       const int32_t nl = (int32_t)group_num_lines(G, i);
       uint64_t k = 0;
       if (!warp_pair_group<T, KV>(base, vbase, G, (uint32_t)i, nl, pivot, ws, phase, k,

@@ -18,6 +18,7 @@ struct TaskScratch {
   uint32_t* bar;       // grid barrier: arrival count, generation
   uint32_t* counts;    // one word per CTA of the partition kernel
   unsigned long long* t_end;  // device time at the end of the last level
+  uint32_t* fetch;     // per level: the next group a warp takes (kMaxLevels words)
 };
 
 // Bytes of TaskScratch for a partition kernel of `grid` CTAs, laid out by
