@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--variant", choices=["smoothed", "strided", "lowspace", "hybrid",
                                           "implicit"],
                     default="smoothed")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-yardstick", action="store_true",
@@ -594,6 +594,8 @@ def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):
     ws = dist_env()[0]
     bytes_all, ms = whole_job(ws, 3 * 8 * n, sum(times) / len(times))  # every rank's array
     return {"value": bytes_all / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "ms_each_step": [round(x, 2) for x in times],
+            "ms_median": float(np.median(times)),
             "h2d_bytes_per_step": 8 * n * ws, "d2h_bytes_per_step": 8 * n * ws, "split": t,
             "path": "lp_partition_host_u64 on a pinned host array (chunked uploads, "
                     "device partitions and copies back overlapping)"}
