@@ -19,10 +19,10 @@
 namespace lp {
 
 // ---------------------------------------------------------------- constants
-// The streaming kernels give one warp one group (the paper's "serial
-// partition of U_i", one processor per group).  A warp holds two lines of its
-// group in registers (the paper's `low` and `high` ends) and keeps kQ more
-// lines in flight per side in shared memory.
+// The streaming kernels give a group to one warp at a time (the paper's
+// "serial partition of U_i", one processor per group).  A warp holds two
+// lines of its group in registers (the paper's `low` and `high` ends) and
+// keeps Q more lines in flight per side in shared memory.
 constexpr uint32_t kLineBytesMax = 2048;   // largest line in key bytes (over all key types)
 // largest line of a key type: 2 KB (fewer, longer line pairs per key; the
 // kernels cap their registers so that two CTAs share an SM)
@@ -120,9 +120,10 @@ LP_HD uint64_t group_split_pos(const StepGeom& G, uint64_t i, uint64_t nl, uint6
 }
 
 // ------------------------------------------------------------ parameter rule
-// Line size b and group count g of one step on n keys of key_bytes each, with
-// `workers` warps each taking one group: the largest line, one group per warp,
-// but at least kMinChunks chunks (lines per group).  Each level then shrinks
+// Line size b and group count g of one step on n keys of key_bytes each: the
+// largest line, at most `workers` groups (the callers pass the warp count, or
+// a multiple of it when warps take several groups), but at least min_chunks
+// chunks (lines per group).  Each level then shrinks
 // the open range by roughly s / 3 at least; a range the CTAs can hold on chip
 // is finished there instead (the paper's base case).
 struct StepParams { uint64_t b, g; };
