@@ -82,8 +82,10 @@ def test_patterns_u64(ctx, kind, n):
 
 
 @pytest.mark.parametrize("kind", ["uniform", "dup16"])
-@pytest.mark.parametrize("n", [1, 4096, 4097, 100003, 1 << 20])
+@pytest.mark.parametrize("n", [1, 4096, 4097, 100003, 1 << 20, 1 << 25])
 def test_u32(ctx, kind, n):
+    # 2^25 keys: the first levels leave open ranges that several CTAs finish
+    # on chip at once (the batched engine's multi-CTA finish for 4-byte keys)
     run_and_compare(ctx, make(kind, n, 31 + n, np.uint32))
 
 
