@@ -71,6 +71,9 @@ def parse():
                     help="partition (default): one 2^30-key partition; quicksort: 2^28 uint64 "
                          "sort; batched: 4096 partitions of log-uniform sizes in one graph; "
                          "serve: Poisson stream of partition and sort requests")
+    ap.add_argument("--pivot-samples", type=int, choices=[3, 15], default=3,
+                    help="quicksort: pivot = median of this many seeded keys (3 per the "
+                         "workload's definition)")
     ap.add_argument("--input", choices=["uniform", "sorted", "reverse", "dup16"],
                     default="uniform", help="quicksort input")
     ap.add_argument("--instances", type=int, default=4096, help="batched: instance count")
@@ -690,7 +693,7 @@ def run_quicksort(args):
     seed0 = args.seed + 7919 * rank
     for w in range(args.warmup):
         fill_sort_input(lp, keys, args.input, seed0 + 100000 + w)
-        lp.lp_quicksort(ctx, keys, seed=w)
+        lp.lp_quicksort(ctx, keys, seed=w, pivot_samples=args.pivot_samples)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -704,7 +707,7 @@ def run_quicksort(args):
         fill_sort_input(lp, keys, args.input, seed0 + k)  # untimed; 2 GiB > L2
         torch.cuda.synchronize()
         ev0.record(stream)
-        lp.lp_quicksort(ctx, keys, seed=k)
+        lp.lp_quicksort(ctx, keys, seed=k, pivot_samples=args.pivot_samples)
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
@@ -734,6 +737,7 @@ def run_quicksort(args):
         "data": "synthetic (SplitMix64 uniform keys, seeded; sorted / reverse / mod 16 "
                 "derived from them)",
         "config": {"workload": "quicksort u64 n=2^%d input=%s" % (args.log2n, args.input),
+                   "pivot": "median of %d seeded keys per subarray" % args.pivot_samples,
                    "n": n, "input": args.input,
                    "l2": "2 GiB input, regenerated on device between steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -764,7 +768,7 @@ def run_quicksort(args):
         for k in range(max(1, args.e2e_steps)):
             ev0.record(stream)
             keys.copy_(host_in, non_blocking=True)
-            lp.lp_quicksort(ctx, keys, seed=k)
+            lp.lp_quicksort(ctx, keys, seed=k, pivot_samples=args.pivot_samples)
             host_out.copy_(keys, non_blocking=True)
             ev1.record(stream)
             ev1.synchronize()

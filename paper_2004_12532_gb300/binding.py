@@ -126,6 +126,8 @@ _SIGS = {
     "lp_ctx_set_batch_tuning": (_i, [_p, _p]),
     "lp_quicksort_u64": (_i, [_p, _p, _u64, _u64, _p]),
     "lp_quicksort_u32": (_i, [_p, _p, _u64, _u64, _p]),
+    "lp_quicksort_ex_u64": (_i, [_p, _p, _u64, _u64, _u32, _p]),
+    "lp_quicksort_ex_u32": (_i, [_p, _p, _u64, _u64, _u32, _p]),
     "lp_ctx_sort_stats": (_i, [_p, _p]),
     "lp_ctx_last_batch_keys": (_i, [_p, _pu64]),
     "lp_batch_streamed_keys": (_i, [_p, _p, _pu64]),
@@ -420,12 +422,17 @@ def lp_ctx_set_batch_tuning(ctx, ctas=0, line_bytes=0, min_chunks=0, group_worke
     ctx.check(lib().lp_ctx_set_batch_tuning(ctx.h, C.byref(t)))
 
 
-def lp_quicksort(ctx, keys, seed=0, stream=None):
-    """Sort a uint64 or uint32 device tensor ascending in place."""
+def lp_quicksort(ctx, keys, seed=0, stream=None, pivot_samples=3):
+    """Sort a uint64 or uint32 device tensor ascending in place; each pivot is
+    the median of pivot_samples (3 or 15) seeded keys."""
     bits = keys.element_size() * 8
     p, n = _dev_ptr(keys, bits)
-    f = lib().lp_quicksort_u64 if bits == 64 else lib().lp_quicksort_u32
-    ctx.check(f(ctx.h, p, n, int(seed), _stream(stream)))
+    if pivot_samples == 3:
+        f = lib().lp_quicksort_u64 if bits == 64 else lib().lp_quicksort_u32
+        ctx.check(f(ctx.h, p, n, int(seed), _stream(stream)))
+    else:
+        f = lib().lp_quicksort_ex_u64 if bits == 64 else lib().lp_quicksort_ex_u32
+        ctx.check(f(ctx.h, p, n, int(seed), int(pivot_samples), _stream(stream)))
 
 
 def lp_lowspace_partition(ctx, keys, pivot, B=4096, base_keys=0, stream=None):

@@ -307,10 +307,13 @@ lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t cou
 namespace {
 
 template <typename T>
-lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, cudaStream_t stream) {
+lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, uint32_t samples,
+                         cudaStream_t stream) {
   if (!c) return LP_ERR_INVALID_ARG;
   c->err.clear();
   c->last_launches = 0;
+  if (samples != 3 && samples != 15)
+    return lp_fail(c, LP_ERR_INVALID_ARG, "pivot samples must be 3 or 15");
   if (n > 0 && !keys) return lp_fail(c, LP_ERR_INVALID_ARG, "null array");
   if ((reinterpret_cast<uintptr_t>(keys) % sizeof(T)) != 0)
     return lp_fail(c, LP_ERR_INVALID_ARG, "array not aligned");
@@ -329,7 +332,7 @@ lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, cudaStre
   if (c->timing && (ls = ensure_events(c)) != LP_OK) return ls;
   if ((ls = ensure_staging(c, lp::quicksort_staging_bytes(n))) != LP_OK) return ls;
   lp::SortStats ss{};
-  e = lp::launch_quicksort<T>(keys, n, seed, c->d_var, c->h_batch, tune, c->task.bar,
+  e = lp::launch_quicksort<T>(keys, n, seed, samples, c->d_var, c->h_batch, tune, c->task.bar,
                               c->task.status, cfg, c->timing ? c->ev : nullptr, &ss);
   c->last_launches = cfg.launches;
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "quicksort");
@@ -427,12 +430,22 @@ lp_status lp_batch_round_stats(lp_batch* b, cudaStream_t stream, lp_batch_rounds
 
 lp_status lp_quicksort_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,
                            cudaStream_t stream) {
-  return quicksort_impl<uint64_t>(c, keys, n, seed, stream);
+  return quicksort_impl<uint64_t>(c, keys, n, seed, 3, stream);
 }
 
 lp_status lp_quicksort_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint64_t seed,
                            cudaStream_t stream) {
-  return quicksort_impl<uint32_t>(c, keys, n, seed, stream);
+  return quicksort_impl<uint32_t>(c, keys, n, seed, 3, stream);
+}
+
+lp_status lp_quicksort_ex_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,
+                              uint32_t pivot_samples, cudaStream_t stream) {
+  return quicksort_impl<uint64_t>(c, keys, n, seed, pivot_samples, stream);
+}
+
+lp_status lp_quicksort_ex_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint64_t seed,
+                              uint32_t pivot_samples, cudaStream_t stream) {
+  return quicksort_impl<uint32_t>(c, keys, n, seed, pivot_samples, stream);
 }
 
 }  // extern "C"

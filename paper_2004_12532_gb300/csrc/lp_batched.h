@@ -105,9 +105,11 @@ struct SortStats {
 size_t quicksort_scratch_bytes(uint64_t n);
 size_t quicksort_staging_bytes(uint64_t n);
 
+// `samples`: pivot = the median of 3 or 15 seeded keys per subarray.
 template <typename T>
-cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* staging,
-                             const BatchTuning& tune, uint32_t* bar, uint32_t* status,
-                             LaunchCfg& cfg, const cudaEvent_t* ev, SortStats* stats);
+cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t samples, void* scratch,
+                             void* staging, const BatchTuning& tune, uint32_t* bar,
+                             uint32_t* status, LaunchCfg& cfg, const cudaEvent_t* ev,
+                             SortStats* stats);
 
 }  // namespace lp

@@ -18,6 +18,25 @@ __device__ __forceinline__ T qs_ld(const T* p) {
   else return (T)__ldcg(reinterpret_cast<const unsigned int*>(p));
 }
 
+// The median of NS keys at seeded positions of keys[lo, lo + n): all loads
+// first, then an insertion sort in registers (fully unrolled).
+template <uint32_t NS, typename T>
+__device__ __forceinline__ T qs_median(const T* keys, uint64_t lo, uint64_t n, uint64_t h) {
+  T v[NS];
+#pragma unroll
+  for (uint32_t j = 0; j < NS; j++) v[j] = qs_ld(&keys[lo + range_of(sm_stream(h, j), n)]);
+#pragma unroll
+  for (uint32_t j = 1; j < NS; j++) {
+#pragma unroll
+    for (uint32_t r = j; r > 0; r--) {
+      const T a = v[r - 1] < v[r] ? v[r - 1] : v[r], b = v[r - 1] < v[r] ? v[r] : v[r - 1];
+      v[r - 1] = a;
+      v[r] = b;
+    }
+  }
+  return v[NS / 2];
+}
+
 // Segment records of every job slice: blockIdx.y = job, x = item.
 template <typename T>
 __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
@@ -33,24 +52,11 @@ __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
   if (q.eq) {
     d.pivot = q.pivot - 1;  // q.pivot > 0: a zero pivot never makes an equal-key item
   } else {
-    // the median of kQsSamples keys at seeded positions: all loads first,
-    // then an insertion sort in registers (fully unrolled)
-    T v[kQsSamples];
-#pragma unroll
-    for (uint32_t j = 0; j < kQsSamples; j++)
-      v[j] = qs_ld(&keys[q.lo + range_of(sm_stream(h, j), q.n)]);
-#pragma unroll
-    for (uint32_t j = 1; j < kQsSamples; j++) {
-#pragma unroll
-      for (uint32_t r = j; r > 0; r--) {
-        const T lo = v[r - 1] < v[r] ? v[r - 1] : v[r], hi = v[r - 1] < v[r] ? v[r] : v[r - 1];
-        v[r - 1] = lo;
-        v[r] = hi;
-      }
-    }
-    d.pivot = (uint64_t)v[kQsSamples / 2];
+    d.pivot = (uint64_t)(J.samples == kQsSamplesMax ? qs_median<kQsSamplesMax>(keys, q.lo, q.n, h)
+                                                    : qs_median<3>(keys, q.lo, q.n, h));
   }
-  d.salt = sm_stream(h, kQsSamples);  // the subarray and level name it, not its place in the list
+  // the subarray and level name it, not its place in the list
+  d.salt = sm_stream(h, kQsSamplesMax + 1);
   segs[J.seg_base + i] = d;
 }
 

@@ -5,7 +5,7 @@
 //
 // A sort job owns an item list per level.  An item is an open subarray
 // [lo, lo + n) with n > kQsCut:
-//   normal item: partitioned by [x <= p], p the median of kQsSamples keys at
+//   normal item: partitioned by [x <= p], p the median of 3 (or 15) keys at
 //                seeded positions; children of at most kQsCut keys go to the job's
 //                small list, larger ones to the next level's list; if no key
 //                exceeds p (t = n) and p > 0, the subarray comes back at the
@@ -26,7 +26,7 @@ namespace lp {
 
 constexpr uint64_t kQsCut = 4096;  // subarrays this small are sorted in shared memory
 constexpr uint32_t kQsSortThreads = 256;
-constexpr uint32_t kQsSamples = 15;  // pivot = the median of this many seeded keys
+constexpr uint32_t kQsSamplesMax = 15;  // pivot samples per subarray, at most
 
 struct QsItem {
   uint64_t lo, n, pivot;  // pivot: of an equal-key item only
@@ -52,11 +52,11 @@ struct QsJob {
   uint32_t level;                  // the job's current level
   uint32_t count;                  // items in this slice
   uint32_t seg_base;               // index of the slice's first segment record
-  uint32_t pad;
+  uint32_t samples;                // pivot: median of this many seeded keys (3 or 15; 0: 3)
 };
 
 // Segment records of every job in `jobs` (grid.y = jobs, x covers the
-// largest item count): median-of-kQsSamples pivots, equal-key pivots minus one.
+// largest item count): median-of-3 (or -15) pivots, equal-key pivots minus one.
 template <typename T>
 cudaError_t launch_qs_build(const QsJob* jobs, uint32_t njobs, uint32_t max_count, SegDesc* segs,
                             cudaStream_t st);

@@ -5,7 +5,7 @@
 // and the subarrays of at most kQsCut keys are sorted by one CTA each in
 // shared memory (kernels in lp_qs.cuh).
 //
-// Per level: build the segment records (median-of-15 pivots), one batched
+// Per level: build the segment records (median-of-3 or -15 pivots), one batched
 // launch per slice of at most kSlice subarrays, split into children, sort the
 // level's small subarrays, read the next list's size back (one host
 // synchronisation per level).  Auxiliary memory: two item lists of at most
@@ -72,9 +72,10 @@ size_t quicksort_staging_bytes(uint64_t n) {
 }
 
 template <typename T>
-cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, void* staging,
-                             const BatchTuning& tune, uint32_t* bar, uint32_t* status,
-                             LaunchCfg& cfg, const cudaEvent_t* ev, SortStats* stats) {
+cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t samples, void* scratch,
+                             void* staging, const BatchTuning& tune, uint32_t* bar,
+                             uint32_t* status, LaunchCfg& cfg, const cudaEvent_t* ev,
+                             SortStats* stats) {
   cudaStream_t st = cfg.stream;
   *stats = SortStats{};
   if (n < 2) return cudaSuccess;
@@ -123,7 +124,7 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
       J.level = levels;
       J.count = (uint32_t)(open > o ? (open - o < L.slice ? open - o : L.slice) : 0);
       J.seg_base = 0;
-      J.pad = 0;
+      J.samples = samples;
     }
     if (levels > 0) e = cudaMemsetAsync(L.lc, 0, sizeof(QsLevelCounts), st);
     if (e == cudaSuccess)
@@ -170,11 +171,11 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, void* scratch, 
   return cudaGetLastError();
 }
 
-template cudaError_t launch_quicksort<uint64_t>(uint64_t*, uint64_t, uint64_t, void*, void*,
-                                                const BatchTuning&, uint32_t*, uint32_t*,
+template cudaError_t launch_quicksort<uint64_t>(uint64_t*, uint64_t, uint64_t, uint32_t, void*,
+                                                void*, const BatchTuning&, uint32_t*, uint32_t*,
                                                 LaunchCfg&, const cudaEvent_t*, SortStats*);
-template cudaError_t launch_quicksort<uint32_t>(uint32_t*, uint64_t, uint64_t, void*, void*,
-                                                const BatchTuning&, uint32_t*, uint32_t*,
+template cudaError_t launch_quicksort<uint32_t>(uint32_t*, uint64_t, uint64_t, uint32_t, void*,
+                                                void*, const BatchTuning&, uint32_t*, uint32_t*,
                                                 LaunchCfg&, const cudaEvent_t*, SortStats*);
 
 }  // namespace lp

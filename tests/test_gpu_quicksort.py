@@ -148,3 +148,21 @@ def test_full_size_2pow28(ctx, kind):
     lp.lp_quicksort(ctx, d, seed=11)
     got = unsigned_key(d)
     assert torch.equal(got, expect)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "dup16", "sorted"])
+@pytest.mark.parametrize("n", [4097, 300000, (1 << 21) + 333])
+def test_median_of_15_pivots(ctx, kind, n):
+    """lp_quicksort_ex_* with 15 pivot samples: the same sorted output."""
+    host = make(kind, n, 71 + n)
+    d = to_dev(host)
+    lp.lp_quicksort(ctx, d, seed=4, pivot_samples=15)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(d, host.dtype), np.sort(host))
+    d32 = to_dev(make("uniform", n, n, np.uint32))
+    ref32 = np.sort(to_host(d32, np.uint32))
+    lp.lp_quicksort(ctx, d32, seed=4, pivot_samples=15)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(d32, np.uint32), ref32)
+    with pytest.raises(lp.LPError):
+        lp.lp_quicksort(ctx, d, pivot_samples=7)
