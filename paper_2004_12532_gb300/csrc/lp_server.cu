@@ -391,7 +391,7 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
     J.level = q.level;
     J.count = (uint32_t)q.open;
     J.seg_base = nsegs[k];
-    J.samples = 3;
+    J.samples = lp::kQsSamplesMax;  // median-of-15 pivots: fewer levels, lower latency
     nsegs[k] += (uint32_t)q.open;
     if (q.open > max_open[k]) max_open[k] = q.open;
     const uint64_t sb = q.open ? 2 * q.open : 1;
