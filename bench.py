@@ -582,25 +582,34 @@ def e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream):
     inside the timed region); the input is restored between steps, untimed.
     The Smoothed Striding variant only (the host call's device partition)."""
     import torch
-    host_in = torch.empty(n, dtype=torch.int64, pin_memory=True)
-    host_work = torch.empty(n, dtype=torch.int64, pin_memory=True)
-    lp.lp_fill_uniform_u64(keys, seed0 + 555)
-    host_in.copy_(keys)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    times, t = [], 0
-    for k in range(max(1, args.e2e_steps) + 1):  # the first call sizes the device copy
-        host_work.copy_(host_in)
+    times, t, err = [], 0, None
+    try:  # pinned memory may run short with many ranks per host: report, don't crash
+        host_in = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        host_work = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        lp.lp_fill_uniform_u64(keys, seed0 + 555)
+        host_in.copy_(keys)
         torch.cuda.synchronize()
-        ev0.record(stream)
-        t = lp.lp_partition_host(ctx, host_work, pivot, seed=k, stream=stream)
-        ev1.record(stream)
-        ev1.synchronize()
-        if k > 0:
-            times.append(ev0.elapsed_time(ev1))
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for k in range(max(1, args.e2e_steps) + 1):  # the first call sizes the device copy
+            host_work.copy_(host_in)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            t = lp.lp_partition_host(ctx, host_work, pivot, seed=k, stream=stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            if k > 0:
+                times.append(ev0.elapsed_time(ev1))
+        del host_in, host_work
+    except (RuntimeError, lp.LPError) as e:
+        err = str(e).splitlines()[0][:200]
     ws = dist_env()[0]
-    bytes_all, ms = whole_job(ws, 3 * 8 * n, sum(times) / len(times))  # every rank's array
+    # every rank joins the reduction; a rank that failed brings an infinite time
+    my_ms = sum(times) / len(times) if times and err is None else float("inf")
+    bytes_all, ms = whole_job(ws, 3 * 8 * n, my_ms)  # every rank's array
+    if not np.isfinite(ms):
+        return {"value": None, "unit": UNIT,
+                "unavailable": err or "another rank's end-to-end leg failed"}
     return {"value": bytes_all / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
             "ms_each_step": [round(x, 2) for x in times],
             "ms_median": float(np.median(times)),
