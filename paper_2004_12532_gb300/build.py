@@ -60,7 +60,8 @@ def _compile(src, extra):
 def _link(target, objs, force):
     if force or _stale(target, objs):
         tmp = target + ".tmp%d" % os.getpid()
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
+        # -ldl: the NVTX ranges look up a profiler's injection library at run time
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -14,6 +14,7 @@
 #include "lp_device.cuh"
 #include "lp_launch.h"
 #include "lp_plan.h"
+#include "lp_trace.h"
 
 lp_status lp_fail(lp_ctx* c, lp_status s, const char* what) {
   if (c) c->err = what;
@@ -425,12 +426,14 @@ lp_status lp_ctx_kernel_ms(lp_ctx* c, float* ms) {
 
 lp_status lp_partition_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
                            lp_variant v, uint64_t seed, cudaStream_t s, uint64_t* split_out) {
+  LP_TRACE("lp_partition_u64");
   if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
   return partition_impl<uint64_t, false>(c, keys, nullptr, n, pivot, v, seed, s, split_out,
                                          nullptr);
 }
 lp_status lp_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
                            lp_variant v, uint64_t seed, cudaStream_t s, uint64_t* split_out) {
+  LP_TRACE("lp_partition_u32");
   if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
   return partition_impl<uint32_t, false>(c, keys, nullptr, n, pivot, v, seed, s, split_out,
                                          nullptr);
@@ -438,6 +441,7 @@ lp_status lp_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot
 lp_status lp_partition_kv_u64(lp_ctx* c, uint64_t* keys, uint64_t* vals, uint64_t n,
                               uint64_t pivot, lp_variant v, uint64_t seed, cudaStream_t s,
                               uint64_t* split_out) {
+  LP_TRACE("lp_partition_kv_u64");
   if (!split_out) return fail(c, LP_ERR_INVALID_ARG, "null split_out");
   return partition_impl<uint64_t, true>(c, keys, vals, n, pivot, v, seed, s, split_out,
                                         nullptr);
@@ -445,6 +449,7 @@ lp_status lp_partition_kv_u64(lp_ctx* c, uint64_t* keys, uint64_t* vals, uint64_
 lp_status lp_partition_u64_async(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
                                  lp_variant v, uint64_t seed, cudaStream_t s,
                                  uint64_t* d_split) {
+  LP_TRACE("lp_partition_u64_async");
   if (!d_split) return fail(c, LP_ERR_INVALID_ARG, "null d_split");
   return partition_impl<uint64_t, false>(c, keys, nullptr, n, pivot, v, seed, s, nullptr,
                                          d_split);
@@ -452,6 +457,7 @@ lp_status lp_partition_u64_async(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t
 lp_status lp_partition_u32_async(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
                                  lp_variant v, uint64_t seed, cudaStream_t s,
                                  uint64_t* d_split) {
+  LP_TRACE("lp_partition_u32_async");
   if (!d_split) return fail(c, LP_ERR_INVALID_ARG, "null d_split");
   return partition_impl<uint32_t, false>(c, keys, nullptr, n, pivot, v, seed, s, nullptr,
                                          d_split);
@@ -459,6 +465,7 @@ lp_status lp_partition_u32_async(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t
 lp_status lp_partition_kv_u64_async(lp_ctx* c, uint64_t* keys, uint64_t* vals, uint64_t n,
                                     uint64_t pivot, lp_variant v, uint64_t seed,
                                     cudaStream_t s, uint64_t* d_split) {
+  LP_TRACE("lp_partition_kv_u64_async");
   if (!d_split) return fail(c, LP_ERR_INVALID_ARG, "null d_split");
   return partition_impl<uint64_t, true>(c, keys, vals, n, pivot, v, seed, s, nullptr, d_split);
 }
@@ -467,6 +474,7 @@ lp_status lp_smoothed_step_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t p
                                uint64_t b, uint64_t g, uint64_t seed, uint64_t level,
                                int strided, cudaStream_t s, uint64_t* vmin, uint64_t* vmax,
                                uint64_t* count) {
+  LP_TRACE("lp_smoothed_step_u64");
   return step_impl<uint64_t>(c, keys, n, pivot, b, g, seed, level, strided, s, vmin, vmax,
                              count);
 }
@@ -474,6 +482,7 @@ lp_status lp_smoothed_step_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t p
                                uint64_t b, uint64_t g, uint64_t seed, uint64_t level,
                                int strided, cudaStream_t s, uint64_t* vmin, uint64_t* vmax,
                                uint64_t* count) {
+  LP_TRACE("lp_smoothed_step_u32");
   return step_impl<uint32_t>(c, keys, n, pivot, b, g, seed, level, strided, s, vmin, vmax,
                              count);
 }
@@ -481,30 +490,36 @@ lp_status lp_smoothed_step_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t p
 lp_status lp_lowspace_partition_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
                                     uint64_t B, uint64_t base_keys, cudaStream_t s,
                                     uint64_t* split_out) {
+  LP_TRACE("lp_lowspace_partition_u64");
   return lowspace_impl<uint64_t>(c, keys, n, pivot, B, base_keys, s, split_out);
 }
 lp_status lp_lowspace_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
                                     uint64_t B, uint64_t base_keys, cudaStream_t s,
                                     uint64_t* split_out) {
+  LP_TRACE("lp_lowspace_partition_u32");
   return lowspace_impl<uint32_t>(c, keys, n, pivot, B, base_keys, s, split_out);
 }
 
 lp_status lp_lowspace_implicit_partition_u64(lp_ctx* c, uint64_t* keys, uint64_t n,
                                              uint64_t pivot, uint64_t B, uint64_t base_keys,
                                              cudaStream_t s, uint64_t* split_out) {
+  LP_TRACE("lp_lowspace_implicit_partition_u64");
   return implicit_impl<uint64_t>(c, keys, n, pivot, B, base_keys, 0, s, split_out);
 }
 lp_status lp_lowspace_implicit_partition_u32(lp_ctx* c, uint32_t* keys, uint64_t n,
                                              uint32_t pivot, uint64_t B, uint64_t base_keys,
                                              cudaStream_t s, uint64_t* split_out) {
+  LP_TRACE("lp_lowspace_implicit_partition_u32");
   return implicit_impl<uint32_t>(c, keys, n, pivot, B, base_keys, 0, s, split_out);
 }
 lp_status lp_lowspace_implicit_prefix_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
                                           uint64_t B, cudaStream_t s, uint64_t* split_out) {
+  LP_TRACE("lp_lowspace_implicit_prefix_u64");
   return implicit_impl<uint64_t>(c, keys, n, pivot, B, 0, 1, s, split_out);
 }
 lp_status lp_lowspace_implicit_prefix_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
                                           uint64_t B, cudaStream_t s, uint64_t* split_out) {
+  LP_TRACE("lp_lowspace_implicit_prefix_u32");
   return implicit_impl<uint32_t>(c, keys, n, pivot, B, 0, 1, s, split_out);
 }
 

@@ -11,6 +11,7 @@
 #include "lp_ctx.h"
 #include "lp_plan.h"
 #include "lp_device.cuh"
+#include "lp_trace.h"
 
 struct lp_batch {
   lp_ctx* ctx = nullptr;
@@ -94,6 +95,7 @@ lp_status lp_ctx_set_batch_tuning(lp_ctx* c, const lp_batch_tuning* t) {
 
 lp_status lp_partition_batched_u64(lp_ctx* c, const lp_segment_u64* segs, uint32_t count,
                                    uint64_t seed, cudaStream_t stream, uint64_t* d_splits) {
+  LP_TRACE("lp_partition_batched_u64");
   if (!c) return LP_ERR_INVALID_ARG;
   c->err.clear();
   c->last_launches = 0;
@@ -205,6 +207,7 @@ lp_status lp_batch_create(lp_ctx* c, const lp_segment_u64* segs, uint32_t count,
 }
 
 lp_status lp_batch_launch(lp_batch* b, cudaStream_t stream) {
+  LP_TRACE("lp_batch_launch");
   if (!b) return LP_ERR_INVALID_ARG;
   if (b->count == 0) return LP_OK;
   cudaError_t e = cudaSetDevice(b->ctx->device);
@@ -240,6 +243,7 @@ lp_status lp_batch_destroy(lp_batch* b) {
 
 lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t count,
                                   cudaStream_t stream, lp_batch_tuning* best) {
+  LP_TRACE("lp_autotune_batched_u64");
   if (!c || (count && !sizes)) return LP_ERR_INVALID_ARG;
   c->err.clear();
   cudaError_t e = cudaSetDevice(c->device);
@@ -430,21 +434,25 @@ lp_status lp_batch_round_stats(lp_batch* b, cudaStream_t stream, lp_batch_rounds
 
 lp_status lp_quicksort_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,
                            cudaStream_t stream) {
+  LP_TRACE("lp_quicksort_u64");
   return quicksort_impl<uint64_t>(c, keys, n, seed, 3, stream);
 }
 
 lp_status lp_quicksort_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint64_t seed,
                            cudaStream_t stream) {
+  LP_TRACE("lp_quicksort_u32");
   return quicksort_impl<uint32_t>(c, keys, n, seed, 3, stream);
 }
 
 lp_status lp_quicksort_ex_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t seed,
                               uint32_t pivot_samples, cudaStream_t stream) {
+  LP_TRACE("lp_quicksort_ex_u64");
   return quicksort_impl<uint64_t>(c, keys, n, seed, pivot_samples, stream);
 }
 
 lp_status lp_quicksort_ex_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint64_t seed,
                               uint32_t pivot_samples, cudaStream_t stream) {
+  LP_TRACE("lp_quicksort_ex_u32");
   return quicksort_impl<uint32_t>(c, keys, n, seed, pivot_samples, stream);
 }
 

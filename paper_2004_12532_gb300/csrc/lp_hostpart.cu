@@ -17,6 +17,7 @@
 #include "lp_device.cuh"
 #include "lp_hostpart.h"
 #include "lp_launch.h"
+#include "lp_trace.h"
 
 namespace lp {
 
@@ -220,11 +221,13 @@ extern "C" {
 
 lp_status lp_partition_host_u64(lp_ctx* c, uint64_t* keys, uint64_t n, uint64_t pivot,
                                 uint64_t seed, cudaStream_t stream, uint64_t* split_out) {
+  LP_TRACE("lp_partition_host_u64");
   return lp::host_partition<uint64_t>(c, keys, n, pivot, seed, stream, split_out);
 }
 
 lp_status lp_partition_host_u32(lp_ctx* c, uint32_t* keys, uint64_t n, uint32_t pivot,
                                 uint64_t seed, cudaStream_t stream, uint64_t* split_out) {
+  LP_TRACE("lp_partition_host_u32");
   return lp::host_partition<uint32_t>(c, keys, n, pivot, seed, stream, split_out);
 }
 

@@ -28,6 +28,7 @@
 #include "lp_device.cuh"
 #include "lp_qs.cuh"
 #include "lp_sched.h"
+#include "lp_trace.h"
 
 namespace {
 
@@ -655,6 +656,7 @@ lp_status lp_server_submit(lp_server* s, const lp_request* r, uint64_t* id_out) 
 }
 
 lp_status lp_server_step(lp_server* s, uint32_t* in_flight) {
+  LP_TRACE("lp_server_step");
   if (!s) return LP_ERR_INVALID_ARG;
   if (s->broken) return srv_fail(s, LP_ERR_CUDA, "server stopped after an error");
   cudaError_t e = cudaSetDevice(s->ctx->device);
@@ -729,6 +731,7 @@ lp_status lp_server_streamed_keys(lp_server* s, uint64_t* keys_u64, uint64_t* ke
 
 lp_status lp_server_run(lp_server* s, const lp_request* reqs, uint32_t count, uint32_t mode,
                         lp_completion* out) {
+  LP_TRACE("lp_server_run");
   if (!s || (count && (!reqs || !out))) return LP_ERR_INVALID_ARG;
   if (s->broken) return srv_fail(s, LP_ERR_CUDA, "server stopped after an error");
   cudaError_t e = cudaSetDevice(s->ctx->device);
