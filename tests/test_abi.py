@@ -58,3 +58,26 @@ def test_builds_for_sm103a_only():
     # the one target architecture of every compile (no PTX for other targets)
     from paper_2004_12532_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/libpartition.h compiles as C99 and as C++17 (a C ABI: plain
+    pointers and sizes, no C++ or torch types), and a C program can take the
+    address of every entry point it declares."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    inc = os.path.join(root, "include")
+    cuda_inc = "/usr/local/cuda/include"
+    names = declared_functions()
+    body = "\n".join("  (void)&%s;" % n for n in names)
+    src = tmp_path / "use.c"
+    src.write_text('#include "libpartition.h"\nint main(void) {\n%s\n  return 0;\n}\n' % body)
+    for cc, std in (("gcc", "-std=c99"), ("g++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            pytest.skip("no %s" % cc)
+        args = [cc, std, "-Wall", "-Werror", "-fsyntax-only", "-I", inc, "-I", cuda_inc]
+        if cc == "g++":
+            args += ["-x", "c++"]
+        r = subprocess.run(args + [str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
