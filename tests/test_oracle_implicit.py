@@ -147,3 +147,16 @@ def test_implicit_partition(n, kind, q):
     assert t == int(np.count_nonzero(a <= p))
     assert np.all(work[:t] <= p) and np.all(work[t:] > p)
     assert np.array_equal(np.sort(work), np.sort(a))
+
+
+def test_bits_for_is_the_bit_length():
+    """L = ceil(log2(n + 1)), the bits of a value in [0, n]: the bit length of
+    n (Python's int.bit_length, an independent definition), at the powers of
+    two and their neighbours and at random sizes."""
+    r = _rng(5)
+    cases = [0, 1, 2, 3, 4, 5, 7, 8, 9] + [(1 << k) + d for k in range(1, 63) for d in (-1, 0, 1)]
+    cases += [int(x) for x in r.integers(0, 2**62, size=200)]
+    for n in cases:
+        assert oracle.bits_for(n) == n.bit_length(), n
+        # the smallest L with n < 2^L, i.e. ceil(log2(n + 1))
+        assert n < (1 << oracle.bits_for(n)) and (n == 0 or n >= (1 << (oracle.bits_for(n) - 1)))
