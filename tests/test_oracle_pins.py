@@ -138,3 +138,20 @@ def test_quicksort_u32(orc):
     expect = np.sort(a)
     orc.quicksort(a, seed=3)
     assert np.array_equal(a, expect)
+
+
+# ---------------------------------------------------------------- count
+def test_count_is_the_predicate_count(orc):
+    """t = #{x <= pivot} (Sec. 2's decider), against numpy's count on random
+    keys of both widths, at pivots that hit a key, miss every key, and sit at
+    the extremes."""
+    r = np.random.default_rng(9)
+    for n in [0, 1, 2, 17, 1000, 65537]:
+        a64 = r.integers(0, 2**64, size=n, dtype=np.uint64)
+        a32 = r.integers(0, 2**32, size=n, dtype=np.uint32)
+        piv64 = [0, 2**64 - 1, 2**63] + ([int(a64[n // 2])] if n else [])
+        piv32 = [0, 2**32 - 1, 2**31] + ([int(a32[n // 2])] if n else [])
+        for p in piv64:
+            assert orc.count(a64, p) == int(np.count_nonzero(a64 <= np.uint64(p)))
+        for p in piv32:
+            assert orc.count(a32, p) == int(np.count_nonzero(a32 <= np.uint32(p)))
