@@ -63,15 +63,17 @@ def test_step_invariants(orc, n, b, g):
     check_step(orc, a0, P50, b, g, X)
 
 
-def test_step_u32(orc):
-    n, b, g = 10000, 16, 24
-    a0 = inputs.uniform_u32(n, 3)
+@pytest.mark.parametrize("n,b,g,q", [(10000, 16, 24, (1, 3)), (4099, 8, 7, (1, 2)),
+                                     (1 << 13, 32, 16, (99, 100)), (777, 5, 9, (1, 100))])
+def test_step_u32(orc, n, b, g, q):
+    """The 4-byte step against the same per-group facts as the 8-byte one:
+    each U_i keeps its multiset, ends predecessors-first, and reports its own
+    k_i and v_i.  Keys span the whole 32-bit range (half of them have the top
+    bit set), so a signed or narrowed compare would miscount some group."""
+    a0 = inputs.uniform_u32(n, 3 + n)
+    assert np.any(a0 >= np.uint32(1 << 31))
     X = orc.draw_X(5, 2, orc.num_chunks(n, b, g), g)
-    a = a0.copy()
-    k, v, vmin, vmax = orc.smoothed_step(a, inputs.quantile_pivot(1, 3, 32), b, g, X)
-    pred = a <= inputs.quantile_pivot(1, 3, 32)
-    assert np.all(pred[:vmin]) and not np.any(pred[vmax:])
-    assert np.array_equal(np.sort(a), np.sort(a0))
+    check_step(orc, a0, inputs.quantile_pivot(q[0], q[1], 32), b, g, X)
 
 
 def test_v_locality(orc):
