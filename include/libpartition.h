@@ -57,7 +57,8 @@ typedef enum {
 } lp_status;
 
 typedef enum {
-  LP_SMOOTHED = 0, /* Recursive Smoothed Striding (Sec. 4) */
+  LP_SMOOTHED = 0, /* Recursive Smoothed Striding (Sec. 4); a range the recursion
+                      fails to shrink goes to LP_LOWSPACE (lp_ctx_set_level_cap) */
   LP_STRIDED = 1,  /* Strided Algorithm: the step with X == 0, then the open
                       range [v_min, v_max) by LP_LOWSPACE (the paper's cleanup is
                       serial) */
@@ -83,9 +84,20 @@ uint64_t lp_ctx_last_launches(const lp_ctx *ctx);
 /* Number of CTAs the streaming kernels use per launch on this device. */
 uint32_t lp_ctx_grid(const lp_ctx *ctx);
 
-/* Partial steps a Smoothed / Strided partition may run (the last one is a
- * single-group finish, the paper's base case). */
+/* Level records of a Smoothed / Strided partition (lp_ctx_level_stats). */
 #define LP_MAX_LEVELS 10
+/* Residual-shrink guard of LP_SMOOTHED (the Hybrid scheme of Sec. 4, Theorem
+ * 4.3, as a fallback): the recursion hands the range it has left open to the
+ * Blocked-Prefix-Sum partition (LP_LOWSPACE, B = 4096) once two levels, each
+ * with fresh offsets X, have each left at least 7/8 of the range before them
+ * open, or when a range is still open at level `levels` (1 .. LP_MAX_LEVELS - 1;
+ * 0 restores the default, LP_MAX_LEVELS - 1).  The result is the same
+ * partition (split and sides) whichever path finishes it; a small cap forces
+ * the handoff, which is how tests reach it.  Applies to later LP_SMOOTHED
+ * calls on ctx with arrays too large to finish on chip at once; those calls
+ * hold the low-space counters (8 bytes per 4096 keys) in ctx.
+ * LP_ERR_INVALID_ARG for levels >= LP_MAX_LEVELS. */
+lp_status lp_ctx_set_level_cap(lp_ctx *ctx, uint32_t levels);
 /* enable != 0: later partition calls on ctx record a CUDA event on their
  * stream before each partial-step kernel and after the last one. */
 lp_status lp_ctx_set_timing(lp_ctx *ctx, int enable);
@@ -98,7 +110,8 @@ lp_status lp_ctx_wait(lp_ctx *ctx);
  * recursion of Sec. 4 on [v_min, v_max)): for level L < LP_MAX_LEVELS,
  * ranges[4L..4L+3] = {lo, hi, b, g} of the range that level partitioned
  * (all zero for a level that had nothing left to do; g == 0 marks the on-chip
- * base case), and ms[L] = the level's duration in milliseconds from device
+ * base case, g == UINT64_MAX a range handed to the low-space partition by the
+ * residual-shrink guard), and ms[L] = the level's duration in milliseconds from device
  * timestamps (ms may be NULL).  After an LP_LOWSPACE call (or
  * lp_lowspace_partition_*) the entries are its phases instead: ms[0..4] =
  * count, MakeSuccessorHeavy, block prefix, innermost prefix on chip, Reorder,
@@ -128,7 +141,10 @@ lp_status lp_partition_kv_u64(lp_ctx *ctx, uint64_t *keys, uint64_t *vals, uint6
                               uint64_t pivot, lp_variant variant, uint64_t seed,
                               cudaStream_t stream, uint64_t *split_out);
 /* As above without synchronising: t is written to the device word *d_split
- * when the stream reaches the end of the call. */
+ * when the stream reaches the end of the call (UINT64_MAX, never a valid
+ * split, after a device-side failure; lp_ctx_wait reports which).  An LP_SMOOTHED
+ * call on an array too large to finish on chip may first grow ctx's scratch
+ * (the residual-shrink guard's counters), which synchronises `stream` once. */
 lp_status lp_partition_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t pivot,
                                  lp_variant variant, uint64_t seed, cudaStream_t stream,
                                  uint64_t *d_split);
@@ -474,10 +490,18 @@ lp_status lp_smoothed_step_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t
  * device memory is entirely held by a framework's caching pool.  Such callers
  * cannot create an lp_ctx, which allocates its scratch.
  *
- * lp_partition_u64_noalloc runs the same kernels as lp_partition_u64_async
- * (LP_SMOOTHED or LP_STRIDED) on the current device and writes the split t to
- * the device word *d_split when the stream gets there; it calls no
- * cudaMalloc, cudaFree or other allocating routine.  Its scratch (the
+ * lp_partition_u64_noalloc partitions keys[0..n) on the current device with the
+ * Recursive Smoothed Striding kernels of lp_partition_u64_async and writes the
+ * split t to the device word *d_split when the stream gets there; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Variants: LP_SMOOTHED, as
+ * lp_partition_u64_async except that a range still open at the last level is
+ * finished by one group (one warp) instead of being handed to the low-space
+ * partition, whose counters grow with n and have no room here; LP_STRIDED, the
+ * Strided Algorithm's first step (X == 0) followed by the same Smoothed
+ * Striding recursion on its open range -- not lp_partition_u64_async's
+ * LP_STRIDED, which cleans that range with the low-space partition.  Both give
+ * the same split and the same two sides (as multisets) as every other
+ * partition of the array.  Its scratch (the
  * per-level descriptors, a status word, a grid barrier and one word per CTA
  * of the launch: about 2 KB on a 152-SM GPU, independent of n) lives in one
  * file-scope __device__ array of LP_NOALLOC_SCRATCH_BYTES bytes, which every
@@ -487,7 +511,8 @@ lp_status lp_smoothed_step_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint32_t
  * device share the one array: calls whose work overlaps on the GPU (other
  * streams, or graphs launched concurrently) race on it and must be
  * serialised by the caller.  Each call re-initialises the scratch it reads.
- * Device-side status (a timed-out wait) is not reported; argument errors are
+ * A device-side failure (a bounded wait that gave up) leaves *d_split =
+ * UINT64_MAX, never a valid split; argument errors are
  * LP_ERR_INVALID_ARG, and so is a device whose launch grid would need more
  * scratch than the array holds (more than about 700 CTAs); CUDA failures are
  * LP_ERR_CUDA. */

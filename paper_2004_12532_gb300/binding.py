@@ -98,6 +98,7 @@ _SIGS = {
     "lp_ctx_level_stats": (_i, [_p, _pu64, C.POINTER(C.c_float), C.POINTER(_i)]),
     "lp_ctx_kernel_ms": (_i, [_p, C.POINTER(C.c_float)]),
     "lp_ctx_wait": (_i, [_p]),
+    "lp_ctx_set_level_cap": (_i, [_p, _u32]),
     "lp_partition_u64": (_i, [_p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
     "lp_partition_u32": (_i, [_p, _p, _u64, _u32, _i, _u64, _p, _pu64]),
     "lp_partition_kv_u64": (_i, [_p, _p, _p, _u64, _u64, _i, _u64, _p, _pu64]),
@@ -261,6 +262,11 @@ class Ctx:
 
     def set_timing(self, on=True):
         self.check(lib().lp_ctx_set_timing(self.h, 1 if on else 0))
+
+    def set_level_cap(self, levels=0):
+        """lp_ctx_set_level_cap: level at which LP_SMOOTHED hands an open range
+        to the low-space partition (0: the last level)."""
+        self.check(lib().lp_ctx_set_level_cap(self.h, int(levels)))
 
     def kernel_ms(self):
         """Event-timed duration of the last timed call's partition kernel (ms)."""

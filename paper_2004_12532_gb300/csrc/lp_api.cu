@@ -133,7 +133,16 @@ lp_status partition_impl(lp_ctx* c, T* keys, uint64_t* vals, uint64_t n, T pivot
   c->last_stream = stream;
   const bool small = n <= lp::small_limit(sizeof(T), KV);
   if (variant == LP_SMOOTHED || small) {
-    e = lp::launch_smoothed<T, KV>(keys, vals, n, pivot, seed, 0, S, cfg);
+    // scratch for the residual-shrink guard's low-space handoff, when the
+    // array is too large to finish on chip at level 0
+    void* hv = nullptr;
+    if (!small && lp::smoothed_may_hand_off<T, KV>(n, cfg.grid)) {
+      lp_status ls =
+          ensure_var(c, lp::lowspace_scratch_bytes(n, lp::kHandoffBlock, cfg.grid), stream);
+      if (ls != LP_OK) return ls;
+      hv = c->d_var;
+    }
+    e = lp::launch_smoothed<T, KV>(keys, vals, n, pivot, seed, 0, S, cfg, hv, c->level_cap);
   } else if (variant == LP_LOWSPACE) {
     lp_status ls = ensure_var(c, lp::lowspace_scratch_bytes(n, kLowspaceBlock, cfg.grid), stream);
     if (ls != LP_OK) return ls;
@@ -355,6 +364,13 @@ lp_status lp_ctx_set_timing(lp_ctx* c, int enable) {
     if (s != LP_OK) return s;
   }
   c->timing = enable != 0;
+  return LP_OK;
+}
+
+lp_status lp_ctx_set_level_cap(lp_ctx* c, uint32_t levels) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  if (levels >= (uint32_t)lp::kMaxLevels) return fail(c, LP_ERR_INVALID_ARG, "level cap too large");
+  c->level_cap = levels;
   return LP_OK;
 }
 

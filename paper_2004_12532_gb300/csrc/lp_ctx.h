@@ -38,6 +38,7 @@ struct lp_ctx {
   unsigned long long* last_batch_tround = nullptr;   // its round timestamps
   lp_sort_stats sort_stats{};                         // of the last quicksort
   unsigned long long* last_low_tl = nullptr;          // phase stamps of the last LP_LOWSPACE call
+  uint32_t level_cap = 0;    // LP_SMOOTHED: level at which an open range is handed over (0: last)
   void* hostpart = nullptr;  // state of the host-array partition (lp_hostpart.cu)
 };
 

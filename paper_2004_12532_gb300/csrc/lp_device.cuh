@@ -19,6 +19,14 @@ enum : uint32_t {
 // Wall-clock limit of any single wait, in ns (about one second).
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
+// Limit of a grid barrier that follows work on `bytes` bytes which some CTA may
+// stream alone (a one-group step is one warp's partition of a whole range):
+// the fixed limit plus 2 ns per byte, i.e. a floor of 0.5 GB/s for that CTA,
+// so that slow but correct work never gives up.
+__host__ __device__ __forceinline__ uint64_t wait_limit_for_bytes(uint64_t bytes) {
+  return kWaitLimitNs + 2ull * bytes;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -115,10 +123,11 @@ __device__ __forceinline__ void bulk_wait_all() {
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
 // counts arrivals, bar[1] is the generation; both start at zero.  The last
 // CTA to arrive resets the count and advances the generation; the others wait
-// for the generation to change, for at most kWaitLimitNs.  Returns false (in
+// for the generation to change, for at most limit_ns.  Returns false (in
 // every thread of the CTA) if this CTA gave up waiting.
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks,
-                                             unsigned int* flag_smem) {
+                                             unsigned int* flag_smem,
+                                             uint64_t limit_ns = kWaitLimitNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int ok = 1u;
@@ -132,7 +141,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nbl
     } else {
       const uint64_t t0 = global_timer_ns();
       while (*gen == g0) {
-        if (global_timer_ns() - t0 > kWaitLimitNs) { ok = 0u; break; }
+        if (global_timer_ns() - t0 > limit_ns) { ok = 0u; break; }
         __nanosleep(64);
       }
     }

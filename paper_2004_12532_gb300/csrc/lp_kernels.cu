@@ -35,8 +35,8 @@ constexpr uint32_t kLevel0MinChunks = 128;
 
 // ------------------------------------------------------------ scratch layout
 size_t task_scratch_bytes(uint32_t grid) {
-  return sizeof(LevelDesc) * kMaxLevels + 64 /* status */ + 64 /* barrier, t_end */ +
-         ((size_t)grid * 4 + 63) / 64 * 64 /* counts */;
+  return sizeof(LevelDesc) * (kMaxLevels + 1) /* levels, handoff */ + 64 /* status */ +
+         64 /* barrier, t_end */ + ((size_t)grid * 4 + 63) / 64 * 64 /* counts */;
 }
 
 TaskScratch carve_scratch(void* base, uint32_t grid) {
@@ -45,6 +45,8 @@ TaskScratch carve_scratch(void* base, uint32_t grid) {
   TaskScratch S;
   S.desc = reinterpret_cast<LevelDesc*>(p);
   p += sizeof(LevelDesc) * kMaxLevels;
+  S.handoff = reinterpret_cast<LevelDesc*>(p);
+  p += sizeof(LevelDesc);
   S.status = reinterpret_cast<uint32_t*>(p);
   S.split = reinterpret_cast<uint64_t*>(p + 8);
   p += 64;
@@ -59,13 +61,13 @@ TaskScratch carve_scratch(void* base, uint32_t grid) {
 
 __global__ void desc_init_kernel(TaskScratch S) {
   const int t = threadIdx.x;
-  if (t < kMaxLevels) {
-    LevelDesc& d = S.desc[t];
+  if (t <= kMaxLevels) {  // the levels, then the handoff record (empty)
+    LevelDesc& d = t < kMaxLevels ? S.desc[t] : *S.handoff;
     d.vmin = ~0ull;
     d.vmax = 0ull;
     d.count = 0ull;
     d.lo = d.hi = d.b = d.g = d.t_start = 0ull;
-    S.fetch[t] = 0u;
+    if (t < kMaxLevels) S.fetch[t] = 0u;
   }
   if (t == 0) {
     *S.status = 0u;
@@ -91,6 +93,8 @@ struct PartArgs {
   uint64_t pivot, seed;
   int strided;                // level 0 with X == 0 (the Strided Algorithm)
   int max_levels;             // 1: level 0 only, the open range left for a cleanup
+  int handoff;                // 1: a range the recursion cannot finish goes to S.handoff
+  int level_cap;              // with handoff: the level at which an open range is handed over
 };
 
 // The whole recursion in one cooperative launch; see the file comment.
@@ -114,6 +118,8 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
   const uint64_t total_warps = (uint64_t)gridDim.x * R::Warps;
   const uint64_t coop_cap = (uint64_t)gridDim.x * Coop<T, KV>::Keys;
   const T pivot = (T)a.pivot;
+  uint64_t prev_n = 0;  // the range of the level before
+  int stalls = 0;       // levels that left at least 7/8 of the range before them open
 
   for (int L = 0; L < a.max_levels; L++) {
     uint64_t lo, hi;
@@ -152,8 +158,26 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
       break;
     }
 
-    // a Partial Partition Step (parameter rule of lp_plan.h); the last level,
-    // should a range still be open, is one group.  Warps take groups one at a
+    // residual-shrink guard: the open range goes to the low-space partition
+    // (launched after this kernel) at the level cap, or once kShrinkTries
+    // levels, each with fresh offsets X, have failed to shrink it by 1/8;
+    // every CTA sees the same ranges, so all take the same branch
+    if (a.handoff && L > 0) {
+      if (n >= prev_n - prev_n / 8) stalls++;
+      if (L >= a.level_cap || stalls >= kShrinkTries) {
+        if (leader) {
+          S.handoff->vmin = lo;
+          S.handoff->vmax = hi;
+          S.desc[L].b = 0;
+          S.desc[L].g = ~0ull;  // marks the handoff in the level records
+        }
+        break;
+      }
+    }
+    prev_n = n;
+
+    // a Partial Partition Step (parameter rule of lp_plan.h); without a
+    // handoff the last level, should a range still be open, is one group.  Warps take groups one at a
     // time from a counter, so that they finish together.  Level 0 of the
     // recursion has up to kLevel0GroupsPerWarp groups per warp (the tail of a
     // level costs more than the wider open range more groups leave); later
@@ -165,7 +189,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
         wide ? choose_params(n, R::K, workers, R::LineBytes, kLevel0MinChunks)
              : choose_params(n, R::K, workers, R::LineBytes);
     const uint64_t b = P.b;
-    const uint64_t g = (L == kMaxLevels - 1) ? 1 : P.g;
+    const uint64_t g = (!a.handoff && L == kMaxLevels - 1) ? 1 : P.g;
     if (leader) { S.desc[L].b = b; S.desc[L].g = g; }
     const StepGeom G = make_geom(n, b, g, level_seed(a.seed, (uint64_t)L),
                                  (a.strided && L == 0) ? 1 : 0);
@@ -186,7 +210,10 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
         atomicAdd(&S.desc[L].count, (unsigned long long)k);
       }
     }
-    if (!grid_barrier(S.bar, gridDim.x, &bar_flag)) {
+    // a one-group level is one warp's partition of the whole range
+    if (!grid_barrier(S.bar, gridDim.x, &bar_flag,
+                      g == 1 ? wait_limit_for_bytes(n * (R::K + (KV ? 8u : 0u)))
+                             : kWaitLimitNs)) {
       if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout);
       break;
     }
@@ -243,11 +270,18 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) level_kernel(T* keys, u
 // Head keys [0, h) and tail keys [body_end, n) lie outside the 16-byte aligned
 // body that the levels partitioned.  With the body split at m = h + count,
 // every misplaced key is in the head, the tail, or the body between m and the
-// final split t; there are at most a dozen, and one thread swaps them.
+// final split t; there are at most a dozen, and one thread swaps them.  After
+// a failure raised earlier (a wait that gave up) the body's count is partial:
+// nothing is scanned or moved, and the split reads UINT64_MAX, never a valid
+// split.
 template <typename T, bool KV>
 __global__ void finalize_kernel(T* keys, uint64_t* vals, uint64_t n, uint64_t h,
                                 uint64_t body_end, T pivot, TaskScratch S) {
   if (threadIdx.x != 0) return;
+  if (__ldcg(S.status) != 0u) {
+    *S.split = ~0ull;
+    return;
+  }
   const uint64_t cb = S.desc[0].count;
   const uint64_t m = h + cb;
   uint64_t hp = 0, tp = 0;
@@ -333,8 +367,16 @@ cudaError_t streaming_grid(int device, uint32_t* grid) {
 }
 
 template <typename T, bool KV>
+bool smoothed_may_hand_off(uint64_t n, uint32_t grid) {
+  using R = Tr<T, KV>;
+  // the body is at most n keys; the on-chip base case takes it whole at level 0
+  return n > small_limit(R::K, KV) && n > (uint64_t)grid * Coop<T, KV>::Keys + 2 * R::A;
+}
+
+template <typename T, bool KV>
 cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64_t seed,
-                            int strided, const TaskScratch& S, LaunchCfg& cfg) {
+                            int strided, const TaskScratch& S, LaunchCfg& cfg, void* handoff_var,
+                            uint32_t level_cap) {
   using R = Tr<T, KV>;
   cudaStream_t st = cfg.stream;
   const size_t smem = stream_smem_bytes<T, KV>();
@@ -361,12 +403,22 @@ cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64
   uint64_t grid = cfg.grid;
   const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
   if (need < grid) grid = need ? need : 1;
+  // a body the CTAs hold at level 0 is finished on chip: no handoff can occur
+  const bool handoff = handoff_var != nullptr && need > grid;
+  a.handoff = handoff ? 1 : 0;
+  a.level_cap = (level_cap >= 1 && level_cap < (uint32_t)kMaxLevels) ? (int)level_cap
+                                                                     : kMaxLevels - 1;
   if (cfg.events) cudaEventRecord(cfg.events[0], st);
   cudaError_t e = launch_cooperative(partition_kernel<T, KV>, (uint32_t)grid, R::Threads, smem,
                                      st, keys, vals, a, S);
   cfg.launches++;
   if (cfg.events) cudaEventRecord(cfg.events[1], st);
   if (e != cudaSuccess) return e;
+  if (handoff) {  // the range handed over, if any (an empty one returns at once)
+    e = launch_lowspace<T, KV>(keys, vals, 0, 0, body_end - h, S.handoff, pivot, kHandoffBlock,
+                               ~0ull, handoff_var, S, nullptr, cfg);
+    if (e != cudaSuccess) return e;
+  }
   finalize_kernel<T, KV><<<1, 32, 0, st>>>(keys, vals, n, h, body_end, pivot, S);
   cfg.launches++;
   return cudaGetLastError();
@@ -393,6 +445,8 @@ cudaError_t launch_first_level(T* keys, uint64_t* vals, uint64_t n, T pivot, uin
   a.seed = seed;
   a.strided = strided;
   a.max_levels = 1;
+  a.handoff = 0;
+  a.level_cap = kMaxLevels - 1;
   uint64_t grid = cfg.grid;
   const uint64_t need = (body_end - h + Coop<T, KV>::Keys - 1) / Coop<T, KV>::Keys;
   if (need < grid) grid = need ? need : 1;
@@ -475,15 +529,14 @@ cudaError_t launch_iota_u64(uint64_t* d, uint64_t n, cudaStream_t s) {
 template cudaError_t streaming_grid<uint64_t, false>(int, uint32_t*);
 template cudaError_t streaming_grid<uint32_t, false>(int, uint32_t*);
 template cudaError_t streaming_grid<uint64_t, true>(int, uint32_t*);
-template cudaError_t launch_smoothed<uint64_t, false>(uint64_t*, uint64_t*, uint64_t, uint64_t,
-                                                      uint64_t, int, const TaskScratch&,
-                                                      LaunchCfg&);
-template cudaError_t launch_smoothed<uint32_t, false>(uint32_t*, uint64_t*, uint64_t, uint32_t,
-                                                      uint64_t, int, const TaskScratch&,
-                                                      LaunchCfg&);
-template cudaError_t launch_smoothed<uint64_t, true>(uint64_t*, uint64_t*, uint64_t, uint64_t,
-                                                     uint64_t, int, const TaskScratch&,
-                                                     LaunchCfg&);
+#define LP_INST_SMOOTHED(T, KV)                                                               \
+  template cudaError_t launch_smoothed<T, KV>(T*, uint64_t*, uint64_t, T, uint64_t, int,          \
+                                              const TaskScratch&, LaunchCfg&, void*, uint32_t);   \
+  template bool smoothed_may_hand_off<T, KV>(uint64_t, uint32_t);
+LP_INST_SMOOTHED(uint64_t, false)
+LP_INST_SMOOTHED(uint32_t, false)
+LP_INST_SMOOTHED(uint64_t, true)
+#undef LP_INST_SMOOTHED
 #define LP_INST_FIRST(T, KV)                                                                  \
   template cudaError_t launch_first_level<T, KV>(T*, uint64_t*, uint64_t, T, uint64_t, int,       \
                                                  const TaskScratch&, LaunchCfg&, uint64_t*,       \

@@ -19,6 +19,8 @@ struct TaskScratch {
   uint32_t* counts;    // one word per CTA of the partition kernel
   unsigned long long* t_end;  // device time at the end of the last level
   uint32_t* fetch;     // per level: the next group a warp takes (kMaxLevels words)
+  LevelDesc* handoff;  // [vmin, vmax): a range the recursion handed to the low-space
+                       // partition (empty when it finished by itself)
 };
 
 // Bytes of TaskScratch for a partition kernel of `grid` CTAs, laid out by
@@ -42,9 +44,24 @@ constexpr int kLowPhases = 6;
 // Keys-only (KV = false, vals == nullptr) and key+payload (KV = true, T = uint64_t).
 // Full Recursive Smoothed Striding partition (strided != 0: the first step uses
 // X == 0, i.e. the Strided Algorithm's partial step).
+//
+// Residual-shrink guard: with `handoff_var` set (lowspace_scratch_bytes(n,
+// kHandoffBlock, cfg.grid) bytes), a range still open at level `level_cap`
+// (1 .. kMaxLevels - 1; 0: kMaxLevels - 1), or after kShrinkTries levels
+// that each left at least 7/8 of the range before them open, is handed to the
+// Blocked-Prefix-Sum partition (the Hybrid of Sec. 4, Theorem 4.3) launched
+// right after the recursion; it returns at once when nothing was handed over.
+// Without it the last level is one group (one warp partitions what is left).
+constexpr uint64_t kHandoffBlock = 4096;
+constexpr int kShrinkTries = 2;
 template <typename T, bool KV>
 cudaError_t launch_smoothed(T* keys, uint64_t* vals, uint64_t n, T pivot, uint64_t seed,
-                            int strided, const TaskScratch& S, LaunchCfg& cfg);
+                            int strided, const TaskScratch& S, LaunchCfg& cfg,
+                            void* handoff_var = nullptr, uint32_t level_cap = 0);
+// True when a partition of n keys can need the handoff (the array does not fit
+// on chip at level 0).
+template <typename T, bool KV>
+bool smoothed_may_hand_off(uint64_t n, uint32_t grid);
 
 // Blocked-Prefix-Sum partition (lp_lowspace.cu) of keys[lo..hi), or of the
 // range [vmin, vmax) of *range_desc when it is set; the range has at most

@@ -346,6 +346,12 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     if (lo >= hi) { lo = 0; hi = 0; }
   }
   const uint64_t n = hi - lo;
+  // an empty range from a descriptor (nothing was handed over): every CTA
+  // reads the same record, so all leave here together
+  if (a.range_desc && n == 0) {
+    if (leader && a.split) *a.split = 0;
+    return;
+  }
   T* A = keys + lo;
   uint64_t* Y = KV ? vals + lo : nullptr;
   const T pivot = (T)a.pivot;
