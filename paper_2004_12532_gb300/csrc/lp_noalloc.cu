@@ -9,8 +9,11 @@
 // scratch), so this entry point keeps the scratch the partition needs -- the
 // per-level descriptors, a status word, the grid barrier and one count per CTA
 // of the launch, about 2 KB on a 152-SM GPU -- in a file-scope __device__
-// array instead.  It launches the same kernels as lp_partition_u64_async and
-// calls no allocating routine.
+// array instead.  It launches the Smoothed Striding kernels of
+// lp_partition_u64_async and calls no allocating routine.  Without counters
+// for the low-space partition it cannot hand a range over: a range still open
+// at the last level is finished by one group, and LP_STRIDED is the Strided
+// first step followed by the Smoothed Striding recursion.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
