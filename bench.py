@@ -44,7 +44,22 @@ from paper_2004_12532_gb300 import inputs  # noqa: E402
 
 METRIC = "in-place partition GB/s (uint64, n=2^30)"
 UNIT = "GB/s"
-KERNEL_SOURCES = ["lp_smoothed.cuh", "lp_kernels.cu", "lp_plan.h", "lp_device.cuh"]
+HANDOFF = (1 << 64) - 1  # level record of a range handed to the low-space partition
+# The kernel sources each committed ncu summary (profiles/) was taken on; a
+# summary feeds roofline.traffic only while the hash of these files matches.
+PART_SOURCES = ["lp_smoothed.cuh", "lp_kernels.cu", "lp_plan.h", "lp_device.cuh",
+                "lp_coop.cuh", "lp_launch.h"]
+BATCH_SOURCES = ["lp_batched.cu", "lp_batched.h", "lp_smoothed.cuh", "lp_plan.h",
+                 "lp_device.cuh", "lp_coop.cuh"]
+QS_SOURCES = BATCH_SOURCES + ["lp_qs.cu", "lp_qs.cuh", "lp_qs_sort.cuh", "lp_quicksort.cu"]
+# name -> (summary file, kernel sources, machine-readable key of its DRAM bytes per unit)
+PROFILES = {
+    "partition_u64": ("partition_kernel_u64_ncu.txt", PART_SOURCES, "dram_bytes_per_key"),
+    "partition_u32": ("partition_kernel_u64_ncu.txt", PART_SOURCES, "dram_bytes_per_key_u32"),
+    "partition_kv": ("partition_kernel_u64_ncu.txt", PART_SOURCES, "dram_bytes_per_key_kv"),
+    "batched": ("batched_kernel_u64_ncu.txt", BATCH_SOURCES, "dram_bytes_per_streamed_key"),
+    "quicksort": ("quicksort_u64_2p25_ncu.txt", QS_SOURCES, "dram_bytes_per_streamed_key"),
+}
 
 
 def parse():
@@ -83,6 +98,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per s")
     ap.add_argument("--budget-gib", type=float, default=64.0, help="serve: HBM budget")
     ap.add_argument("--slots", type=int, default=256, help="serve: requests in flight, at most")
+    ap.add_argument("--no-subs", action="store_true",
+                    help="default run: skip the other workloads' objects (u32, key+payload, "
+                         "quicksort, batched, serve)")
     return ap.parse_args()
 
 
@@ -93,11 +111,11 @@ def dist_env():
     return ws, rank, local
 
 
-def kernel_hash():
-    """Hash of the partition kernel's sources without // comments and blank
-    lines (a comment changes no kernel)."""
+def kernel_hash(sources=None):
+    """Hash of kernel sources without // comments and blank lines (a comment
+    changes no kernel)."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (sources or PART_SOURCES):
         for line in open(os.path.join(ROOT, "paper_2004_12532_gb300", "csrc", f), "rb"):
             code = line.split(b"//", 1)[0].rstrip()
             if code:
@@ -105,24 +123,26 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n_keys):
-    """dram read+write bytes per level-0 launch from the committed ncu summary,
-    scaled to n_keys, if the summary was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "partition_kernel_u64_ncu.txt")
+def profiled_traffic(name, units):
+    """(DRAM read + write bytes per launch, None) from the committed ncu summary
+    `name`, scaled to `units` (keys of the launch), if that summary was taken on
+    the current kernel sources; else (None, why not)."""
+    fname, sources, key = PROFILES[name]
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
-        return None
+        return None, "no ncu summary committed"
     kv = {}
     for line in open(path):
-        if ":" in line:
+        if ":" in line and not line.startswith(" "):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_sources_sha256_16") != kernel_hash():
-        return None
+    if kv.get("kernel_sources_sha256_16") != kernel_hash(sources):
+        return None, "the kernel changed since its ncu capture"
     try:
-        per_key = float(kv["dram_bytes_per_key"])
+        per_unit = float(kv[key])
     except (KeyError, ValueError):
-        return None
-    return per_key * n_keys
+        return None, "the ncu summary has no %s" % key
+    return per_unit * units, None
 
 
 def measured_peaks():
@@ -185,20 +205,34 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def cpu_oracle_gbs(log2n_sample, pivot, seed, min_seconds=8.0, max_reps=5):
+def cpu_oracle_partition(dt, log2n, pivot, seed, min_seconds):
+    """cpu_baseline of a partition workload: the serial oracle (two-pointer
+    partition; with payloads, key and payload swapped together) on a bounded
+    sample of the same distribution and pivot, one host core."""
     import oracle
-    n = 1 << log2n_sample
+    ls = min(log2n, 27 if dt == "u64" else 26)
+    n = 1 << ls
     times = []
     t_start = time.time()
-    for r in range(max_reps):
-        a = inputs.uniform_u64(n, seed + r)
+    for r in range(5):
+        a = inputs.uniform_u32(n, seed + r) if dt == "u32" else inputs.uniform_u64(n, seed + r)
+        v = np.arange(n, dtype=np.uint64) if dt == "kv" else None
         t0 = time.perf_counter()
-        oracle.partition(a, pivot)
+        if v is None:
+            oracle.partition(a, pivot)
+        else:
+            oracle.partition_kv(a, v, pivot)
         times.append(time.perf_counter() - t0)
         if time.time() - t_start > min_seconds and len(times) >= 2:
             break
     med = statistics.median(times)
-    return 3 * 8 * n / med / 1e9, n, len(times), med
+    E = {"u64": 8, "u32": 4, "kv": 16}[dt]
+    what = {"u64": "uint64 keys", "u32": "uint32 keys",
+            "kv": "uint64 key + uint64 payload pairs"}[dt]
+    return {"value": 3 * E * n / med / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "2^%d %s, same distribution and pivot, median of %d runs (%.2f s each) "
+                      "of the serial two-pointer partition" % (ls, what, len(times), med),
+            "host_cores_available": os.cpu_count()}
 
 
 def cpu_parallel_gbs(log2n, pivot, seed, reps=3):
@@ -246,33 +280,43 @@ def run_reference(args):
                           "unavailable": "the reference arm times uint64 partitions only"}))
         return
     pivot = inputs.quantile_pivot(args.quantile, 100, 64)
-    log2s = min(args.log2n, 26)
-    n = 1 << log2s
+    n = 1 << args.log2n
+    # the full workload: one input generated once, restored before each timed
+    # step (untimed); warm-up steps on a 2^24-key slice of it
+    master = inputs.uniform_u64(n, args.seed)
+    work = np.empty_like(master)
     for w in range(args.warmup):
-        a = inputs.uniform_u64(n, args.seed + 1000 + w)
+        a = master[:1 << min(24, args.log2n)].copy()
         oracle.partition(a, pivot)
     total = 0.0
     for k in range(args.steps):
-        a = inputs.uniform_u64(n, args.seed + k)
+        np.copyto(work, master)
         t0 = time.perf_counter()
-        oracle.partition(a, pivot)
+        oracle.partition(work, pivot)
         total += time.perf_counter() - t0
     ms = total / args.steps * 1e3
     value = 3 * 8 * n / (ms / 1e3) / 1e9
-    sample = "2^%d uint64 keys per step (of the 2^%d workload), same distribution and pivot" % (
-        log2s, args.log2n)
+    sample = ("the whole workload: 2^%d uint64 keys per step, same distribution and pivot "
+              "(one seeded input, restored before each step)" % args.log2n)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "partition u64 n=2^%d pivot at %d%% quantile, %s" % (
-                       args.log2n, args.quantile, args.variant),
-                   "n": 1 << args.log2n, "pivot": pivot, "variant": args.variant,
-                   "dtype": "u64", "oracle": "serial two-pointer partition (CPU)"},
+        "config": partition_config(args, "u64", args.log2n, n, pivot, 1),
+        "reference": "the oracle: serial two-pointer partition (CPU), one host core",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def partition_config(args, dt, log2n, n, pivot, ws):
+    """The config object of a partition workload (both arms print the same)."""
+    return {"workload": "partition %s n=2^%d pivot at %d%% quantile, %s" % (
+                dt, log2n, args.quantile, args.variant),
+            "n": n, "pivot": pivot, "variant": args.variant, "dtype": dt,
+            "l2": "inputs larger than L2 (8 GiB), regenerated on device between steps",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
 
 
 def reference_line(args, metric, value, unit, ms, workload, oracle_kind, sample, dtype="u64"):
@@ -363,17 +407,141 @@ def run_reference_serve(args):
                    "sort can overrun it), service time only", dtype="u32+u64")
 
 
+# ---------------------------------------------------------------- parity
+# In-run checks of a result against properties that hold at any size (the
+# plain definition of the problem): the split equals the predicate count, the
+# postcondition holds, and the array is a permutation of its input, the last
+# by an order-independent fingerprint (two wrapping sums of a 64-bit mixer,
+# Murmur3's finalizer, over every key).  Device-side torch ops, outside the
+# timed regions.
+
+def _s64(c):
+    """A 64-bit constant as the int64 value with the same bits."""
+    c &= (1 << 64) - 1
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+_FM1, _FM2, _FALT = _s64(0xFF51AFD7ED558CCD), _s64(0xC4CEB9FE1A85EC53), _s64(0x9E3779B97F4A7C15)
+_CHUNK = 1 << 27
+
+
+def _bits64(x):
+    """int32 -> int64 with the uint32 value; int64 unchanged."""
+    import torch
+    return (x.to(torch.int64) & 0xFFFFFFFF) if x.dtype == torch.int32 else x
+
+
+def _fmix(x):
+    m = (1 << 31) - 1  # logical shift by 33 on int64 bits
+    x = x ^ ((x >> 33) & m)
+    x = x * _FM1
+    x = x ^ ((x >> 33) & m)
+    x = x * _FM2
+    return x ^ ((x >> 33) & m)
+
+
+def fingerprint(keys, vals=None):
+    """Order-independent fingerprint of a key array (or of its (key, value)
+    pairs): equal for any permutation, different for any other multiset but
+    with negligible probability."""
+    a = b = 0
+    for i in range(0, keys.numel(), _CHUNK):
+        k = _bits64(keys[i:i + _CHUNK])
+        if vals is not None:
+            k = _fmix(k) ^ _fmix(vals[i:i + _CHUNK] ^ _FALT) * 3
+        a = (a + int(_fmix(k).sum().item())) & ((1 << 64) - 1)
+        b = (b + int(_fmix(k ^ _FALT).sum().item())) & ((1 << 64) - 1)
+    return a, b
+
+
+def count_le(keys, pivot):
+    """Keys <= pivot, in the unsigned order of their bits."""
+    c = 0
+    if keys.dtype.itemsize == 4:
+        for i in range(0, keys.numel(), _CHUNK):
+            c += int((_bits64(keys[i:i + _CHUNK]) <= int(pivot)).sum().item())
+        return c
+    pv = _s64(int(pivot) ^ (1 << 63))
+    for i in range(0, keys.numel(), _CHUNK):
+        c += int(((keys[i:i + _CHUNK] ^ _s64(1 << 63)) <= pv).sum().item())
+    return c
+
+
+def partition_holds(keys, t, pivot):
+    """keys[0..t) <= pivot < keys[t..n)."""
+    return count_le(keys[:t], pivot) == t and count_le(keys[t:], pivot) == 0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    init_dist(local, ws)
     from paper_2004_12532_gb300 import binding as lp
+    result = measure_partition(args, lp, args.dtype, args.log2n, extras=True)
+    if (args.dtype == "u64" and args.log2n == 30 and args.variant == "smoothed" and
+            args.quantile == 50 and not args.no_subs):
+        result.update(sub_results(args, lp))
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
-    n = 1 << args.log2n
-    dt = args.dtype
+
+def sub_args(args):
+    """The other workloads of the default run: at most 5 timed steps after at
+    least 3 warm-up steps each, device-timed only (the headline carries e2e)."""
+    import copy
+    a = copy.copy(args)
+    a.steps = max(1, min(args.steps, 5))
+    a.warmup = max(3, min(args.warmup, 3))
+    a.no_e2e = True
+    a.no_yardstick = True
+    return a
+
+
+def sub_results(args, lp):
+    """Every other workload in the default run, one object each: the partition
+    of 2^31 uint32 keys and of 2^29 key + payload pairs, the quicksort of 2^28
+    uint64 keys on its four inputs, the batched partition of 4096 instances and
+    the serving run."""
+    import torch
+    sa = sub_args(args)
+    out = {}
+    torch.cuda.empty_cache()
+    out["u32_2p31"] = measure_partition(sa, lp, "u32", 31)
+    torch.cuda.empty_cache()
+    out["kv_2p29"] = measure_partition(sa, lp, "kv", 29)
+    torch.cuda.empty_cache()
+    qs = {}
+    for inp in ("uniform", "sorted", "reverse", "dup16"):
+        qa = copy_with(sa, input=inp, log2n=28)
+        qs[inp] = measure_quicksort(qa, lp)
+        torch.cuda.empty_cache()
+    out["quicksort_2p28"] = qs
+    out["batched"] = measure_batched(copy_with(sa, instances=4096), lp)
+    torch.cuda.empty_cache()
+    out["serve"] = measure_serve(copy_with(sa, steps=min(sa.steps, 2), warmup=1,
+                                           requests=1000, rate=2000.0), lp)
+    torch.cuda.empty_cache()
+    return out
+
+
+def copy_with(args, **kw):
+    import copy
+    a = copy.copy(args)
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def measure_partition(args, lp, dt, log2n, extras=False):
+    """One partition workload: `dt` keys ("u64", "u32" or "kv": uint64 keys
+    with uint64 payloads), n = 2^log2n, the pivot at args.quantile; returns its
+    JSON object.  extras: the out-of-place yardstick, the e2e leg through the
+    host-array entry point and the CPU baselines (u64 only)."""
+    import torch
+    ws, rank, local = dist_env()
+    n = 1 << log2n
     K = 4 if dt == "u32" else 8          # key bytes
     E = 16 if dt == "kv" else K          # bytes moved per key (key + payload)
     pivot = inputs.quantile_pivot(args.quantile, 100, 32 if dt == "u32" else 64)
@@ -422,12 +590,15 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     part_ms, lvl0_ms, lvl0_n, launches, traffic_keys, kern_ms = [], [], [], 0, [], []
-    levels_seen, level_ms = [], []
+    levels_seen, level_ms, handoffs = [], [], 0
+    pre = None
     barrier()
     wall0 = time.perf_counter()
     clocks.start()
     for k in range(args.steps):
         fill(seed0 + k)
+        if k == args.steps - 1:  # the last step's input, for the parity checks (untimed)
+            pre = (count_le(keys, pivot), fingerprint(keys, vals))
         ev0.record(stream)
         part(k)
         ev1.record(stream)
@@ -438,13 +609,23 @@ def run_ours(args):
         kern_ms.append(ctx.kernel_ms())
         lvl0_ms.append(st[0][4])
         lvl0_n.append(st[0][1] - st[0][0])
-        traffic_keys.append(sum(hi - lo for lo, hi, _, _, _ in st))
+        # a range handed to the low-space partition is not streamed by this kernel
+        traffic_keys.append(sum(hi - lo for lo, hi, _, g, _ in st if g != HANDOFF))
+        handoffs += sum(1 for _, _, _, g, _ in st if g == HANDOFF)
         levels_seen.append([(hi - lo) for lo, hi, _, _, _ in st if hi > lo])
         level_ms.append([ms_ for _, _, _, _, ms_ in st])
     barrier()
     wall_s = time.perf_counter() - wall0
     clk = clocks.stop()
     t = int(d_split.item())
+    parity = {"split_equals_count": t == pre[0],
+              "postcondition": partition_holds(keys, t, pivot),
+              "permutation_fingerprint": fingerprint(keys, vals) == pre[1],
+              "checked": "last timed step: split vs the count of keys <= pivot, "
+                         "keys[0..t) <= pivot < keys[t..n), multiset fingerprint of "
+                         "the %s before and after" % ("(key, payload) pairs" if vals is not
+                                                      None else "keys")}
+    parity["ok"] = all(v for k_, v in parity.items() if k_ != "checked")
 
     ms = sum(part_ms) / len(part_ms)
     bytes_all, ms_all = whole_job(ws, 3 * E * n, ms)
@@ -455,6 +636,7 @@ def run_ours(args):
     k_keys = sum(traffic_keys) / len(traffic_keys)
     kname = {"u64": "uint64_t", "u32": "uint32_t", "kv": "uint64_t, payload"}[dt]
     basis = None
+    traffic_note = None
     if args.variant in ("lowspace", "implicit"):
         # Sec. 5's accounting of the low-space partition: 3.5 read/write passes
         # and 0.5 read pass over the keys, i.e. 7.5 key bytes per key -- derived
@@ -466,11 +648,14 @@ def run_ours(args):
         kernel = "lowspace_kernel<%s%s> (all phases, one cooperative launch)" % (
             kname, ", values in key order" if variant is None else "")
         traffic = None
+        traffic_note = ("not scaled from a small capture: at 2^26 a quarter of the "
+                        "MakeSuccessorHeavy traffic stays in L2, at full size almost none")
     else:
         k_bytes = 2 * E * k_keys  # one read and one write of every key of every level
         kernel = "partition_kernel<%s> (all levels, one cooperative launch)" % kname
-        traffic = profiled_traffic(k_keys) if dt == "u64" and args.variant == "smoothed" \
-            else None
+        traffic, traffic_note = (profiled_traffic("partition_" + dt, k_keys)
+                                 if args.variant == "smoothed"
+                                 else (None, "no capture of this variant"))
     achieved = k_bytes / (k_ms / 1e3) / 1e9
     l0_ms = sum(lvl0_ms) / len(lvl0_ms)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -479,53 +664,49 @@ def run_ours(args):
                 "ms_per_launch": k_ms,
                 "level0_gbs_device_timestamps": 2 * E * (sum(lvl0_n) / len(lvl0_n)) /
                 (l0_ms / 1e3) / 1e9 if l0_ms > 0 else None}
+    if traffic is None and traffic_note:
+        roofline["traffic_note"] = traffic_note
     if basis:
         roofline["basis"] = basis
 
-    metric = METRIC if (dt == "u64" and args.log2n == 30) else \
+    metric = METRIC if (dt == "u64" and log2n == 30) else \
         "in-place partition GB/s (%s, n=2^%d)" % ({"u64": "uint64", "u32": "uint32",
                                                    "kv": "uint64 key + uint64 payload"}[dt],
-                                                  args.log2n)
+                                                  log2n)
     result = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32" if dt == "u32" else "u64",
         "data": "synthetic (SplitMix64 uniform keys, seeded)",
-        "config": {"workload": "partition %s n=2^%d pivot at %d%% quantile, %s" % (
-                       dt, args.log2n, args.quantile, args.variant),
-                   "n": n, "pivot": pivot, "variant": args.variant, "dtype": dt,
-                   "l2": "inputs larger than L2 (8 GiB), regenerated on device between steps",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": partition_config(args, dt, log2n, n, pivot, ws),
         "roofline": roofline,
         "gpu_launches": launches,
+        "parity": parity,
         "split_last_step": t,
-        "true_gbs": ws * 2 * K * (sum(traffic_keys) / len(traffic_keys)) / (ms_all / 1e3) / 1e9,
+        # physical read + write bytes of the partition kernel's levels over the step time
+        "true_gbs": ws * 2 * E * k_keys / (ms_all / 1e3) / 1e9,
         "level_ranges_last_step": levels_seen[-1],
         "level_ms_mean": [round(sum(x) / len(x), 4) for x in zip(*level_ms)],
+        "handoffs": handoffs,
         "aux_bytes": ctx.aux_bytes,
         "wall_s_timed_region": wall_s,
     }
     if clk:
         result["clocks"] = clk
 
-    if not args.no_yardstick and dt == "u64":
+    if extras and not args.no_yardstick and dt == "u64":
         result["yardstick_cub"] = cub_yardstick(args, keys, n, pivot, stream, fill, seed0, t)
-    if not args.no_e2e and dt == "u64" and args.variant == "smoothed":
+        result["yardstick_standard"] = standard_yardstick(args, keys, n, pivot, stream, fill,
+                                                          seed0, t)
+    if extras and not args.no_e2e and dt == "u64" and args.variant == "smoothed":
         result["e2e"] = e2e_leg(args, lp, ctx, keys, d_split, pivot, variant, n, seed0, stream)
-    if rank == 0 and ws == 1 and not args.no_cpu and dt == "u64":
-        result["cpu_parallel"] = cpu_parallel_gbs(min(args.log2n, 27), pivot, args.seed)
-        gbs, ns, reps, med = cpu_oracle_gbs(min(args.log2n, 27), pivot, args.seed)
-        result["cpu_baseline"] = {
-            "value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "2^%d uint64 keys, same distribution and pivot, median of %d runs "
-                      "(%.2f s each) of the serial two-pointer partition" % (
-                          int(np.log2(ns)), reps, med),
-            "host_cores_available": os.cpu_count()}
-    if rank == 0:
-        print(json.dumps(result))
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        if extras and dt == "u64":
+            result["cpu_parallel"] = cpu_parallel_gbs(min(log2n, 27), pivot, args.seed)
+        result["cpu_baseline"] = cpu_oracle_partition(dt, log2n, pivot, args.seed,
+                                                      8.0 if extras else 4.0)
     ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    return result
 
 
 def cub_yardstick(args, keys, n, pivot, stream, fill, seed0, split_ours):
@@ -572,6 +753,55 @@ def cub_yardstick(args, keys, n, pivot, stream, fill, seed0, split_ours):
            "extra_device_bytes": 8 * n + tb.value,
            "same_split": int(sel.item()) == split_ours}
     del out, tmp
+    return res
+
+
+def standard_yardstick(args, keys, n, pivot, stream, fill, seed0, split_ours):
+    """The paper's Standard linear-space partition (Sec. 2: prefix sums S in an
+    array of n counts, reorder into C, copy back; libyardstick.so) of the same
+    input, timed the same way: the high-space baseline of the paper's
+    experiments, on this GPU.  Not the product path."""
+    import ctypes
+    import torch
+    path = os.path.join(ROOT, "paper_2004_12532_gb300", "libyardstick.so")
+    if not os.path.exists(path):
+        return {"unavailable": "libyardstick.so not built"}
+    L = ctypes.CDLL(path)
+    L.yd_standard_scratch_words.restype = ctypes.c_uint64
+    L.yd_standard_scratch_words.argtypes = [ctypes.c_uint64]
+    L.yd_standard_partition_u64.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    words = L.yd_standard_scratch_words(n)
+    scratch = torch.empty(words, dtype=torch.int64, device="cuda")
+    sel = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for k in range(max(3, args.warmup) + max(3, min(args.steps, 5))):
+        fill(seed0 + k)
+        ev0.record(stream)
+        rc = L.yd_standard_partition_u64(keys.data_ptr(), n, pivot, scratch.data_ptr(),
+                                         sel.data_ptr(), stream.cuda_stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        if rc != 0:
+            return {"unavailable": "standard partition failed"}
+        if k >= max(3, args.warmup):
+            times.append(ev0.elapsed_time(ev1))
+    fill(seed0 + args.steps - 1)  # the last timed input of our partition, for the split
+    L.yd_standard_partition_u64(keys.data_ptr(), n, pivot, scratch.data_ptr(), sel.data_ptr(),
+                                stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = sum(times) / len(times)
+    res = {"kernel": "Standard linear-space partition (Sec. 2; prefix phase, reorder into C, "
+                     "copy back)", "ms_per_step": ms,
+           "effective_gbs": 3 * 8 * n / (ms / 1e3) / 1e9,
+           # algorithmic traffic: count pass (8n), prefix pass (read 8n, write S 8n),
+           # reorder (read A and S, write C: 24n), copy back (16n)
+           "algorithmic_gbs": 64 * n / (ms / 1e3) / 1e9,
+           "extra_device_bytes": 8 * words,
+           "same_split": int(sel.item()) == split_ours}
+    del scratch
     return res
 
 
@@ -692,6 +922,18 @@ def run_quicksort(args):
     ws, rank, local = dist_env()
     init_dist(local, ws)
     from paper_2004_12532_gb300 import binding as lp
+    result = measure_quicksort(args, lp)
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_quicksort(args, lp):
+    """The quicksort workload (n = 2^args.log2n uint64 keys, input args.input);
+    returns its JSON object."""
+    import torch
+    ws, rank, local = dist_env()
     n = 1 << args.log2n
     keys = torch.empty(n, dtype=torch.int64, device="cuda")
     ctx = lp.Ctx(local)
@@ -710,10 +952,13 @@ def run_quicksort(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     step_ms, stats, launches = [], [], 0
+    pre = None
     wall0 = time.perf_counter()
     clocks.start()
     for k in range(args.steps):
         fill_sort_input(lp, keys, args.input, seed0 + k)  # untimed; 2 GiB > L2
+        if k == args.steps - 1:
+            pre = fingerprint(keys)
         torch.cuda.synchronize()
         ev0.record(stream)
         lp.lp_quicksort(ctx, keys, seed=k, pivot_samples=args.pivot_samples)
@@ -729,15 +974,36 @@ def run_quicksort(args):
     clk = clocks.stop()
     key = unsigned_order(keys)
     sorted_ok = bool((key[1:] >= key[:-1]).all())
+    parity = {"sorted": sorted_ok, "permutation_fingerprint": fingerprint(keys) == pre,
+              "checked": "last timed step: every key <= the next (unsigned), multiset "
+                         "fingerprint of the keys before and after (the sorted output is "
+                         "unique, so these fix it)"}
+    parity["ok"] = parity["sorted"] and parity["permutation_fingerprint"]
     ms = sum(step_ms) / len(step_ms)
     keys_all, ms_all = whole_job(ws, n, ms)
     value = keys_all / (ms_all / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    pk = sum(s["partition_keys"] for s in stats) / len(stats)
-    pms = sum(s["partition_ms"] for s in stats) / len(stats)
-    sk = sum(s["sort_keys"] for s in stats) / len(stats)
-    sms = sum(s["sort_ms"] for s in stats) / len(stats)
+    pk = sum(s_["partition_keys"] for s_ in stats) / len(stats)
+    pms = sum(s_["partition_ms"] for s_ in stats) / len(stats)
+    sk = sum(s_["sort_keys"] for s_ in stats) / len(stats)
+    sms = sum(s_["sort_ms"] for s_ in stats) / len(stats)
     achieved = 2 * 8 * pk / (pms / 1e3) / 1e9
+    traffic, why = profiled_traffic("quicksort", pk)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "batched_kernel<uint64_t> (every partition level, "
+                          "with its set-up launches)",
+                "peak_kind": peak_kind,
+                "algorithmic_bytes_per_step": 2 * 8 * pk, "ms_per_step": pms,
+                "sort_kernel": {"achieved": 2 * 8 * sk / (sms / 1e3) / 1e9 if sms else None,
+                                "ms_per_step": sms, "keys": sk},
+                # the whole sort: every key streamed by a partition level or sorted
+                # on chip is read and written once (2K bytes), over the step time
+                "whole_sort": {"algorithmic_bytes": 2 * 8 * (pk + sk), "ms": ms,
+                               "achieved": 2 * 8 * (pk + sk) / (ms / 1e3) / 1e9,
+                               "frac": 2 * 8 * (pk + sk) / (ms / 1e3) / 1e9 / peak}}
+    if traffic is None:
+        roofline["traffic_note"] = why
     result = {
         "metric": "quicksort keys/s (uint64, n=2^%d, %s)" % (args.log2n, args.input),
         "value": value, "unit": "Gkeys/s", "n_gpus": ws, "steps": args.steps,
@@ -750,17 +1016,11 @@ def run_quicksort(args):
                    "n": n, "input": args.input,
                    "l2": "2 GiB input, regenerated on device between steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "batched_kernel<uint64_t> (every partition level, "
-                               "with its set-up launches)",
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_step": 2 * 8 * pk, "ms_per_step": pms,
-                     "sort_kernel": {"achieved": 2 * 8 * sk / (sms / 1e3) / 1e9 if sms else None,
-                                     "ms_per_step": sms, "keys": sk}},
+        "roofline": roofline,
         "levels": stats[-1]["levels"],
         "partition_keys_per_key": pk / n,
         "gpu_launches": launches,
+        "parity": parity,
         "sorted_last_step": sorted_ok,
         "aux_bytes": ctx.aux_bytes,
         "wall_s_timed_region": wall_s,
@@ -788,17 +1048,15 @@ def run_quicksort(args):
                          "h2d_bytes_per_step": 8 * n * ws, "d2h_bytes_per_step": 8 * n * ws,
                          "path": "pinned host -> device, lp_quicksort_u64, device -> pinned host"}
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, ns, reps, med = cpu_oracle_sort(args.input, min(args.log2n, 22), args.seed)
+        v, ns, reps, med = cpu_oracle_sort(args.input, min(args.log2n, 22), args.seed,
+                                           min_seconds=2.0 if args.steps <= 5 else 8.0)
         result["cpu_baseline"] = {
             "value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
             "sample": "2^%d uint64 keys, same input kind, median of %d runs (%.2f s each) of "
                       "the serial quicksort" % (int(np.log2(ns)), reps, med),
             "host_cores_available": os.cpu_count()}
-    if rank == 0:
-        print(json.dumps(result))
     ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    return result
 
 
 # ---------------------------------------------------------------- batched
@@ -837,6 +1095,36 @@ def run_batched(args):
     ws, rank, local = dist_env()
     init_dist(local, ws)
     from paper_2004_12532_gb300 import binding as lp
+    result = measure_batched(args, lp)
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def segment_fingerprints(buf, offs, sizes):
+    """One wrapping 64-bit sum of the mixed keys per segment (an
+    order-independent fingerprint of each segment's multiset), from a prefix
+    sum over the whole buffer."""
+    import torch
+    F = torch.empty_like(buf)
+    for i in range(0, buf.numel(), _CHUNK):
+        F[i:i + _CHUNK] = _fmix(buf[i:i + _CHUNK])
+    F.cumsum_(0)
+    ends = torch.tensor([o + int(m) - 1 for o, m in zip(offs, sizes)], device=buf.device)
+    starts = torch.tensor([o - 1 for o in offs], device=buf.device)
+    before = torch.where(starts >= 0, F[starts.clamp(min=0)], torch.zeros_like(starts))
+    out = (F[ends] - before).cpu().tolist()
+    del F
+    return out
+
+
+def measure_batched(args, lp):
+    """The batched workload (args.instances uint64 instances, sizes log-uniform in
+    [2^8, 2^22]) against the same instances as plain launches; returns its JSON
+    object."""
+    import torch
+    ws, rank, local = dist_env()
     count = args.instances
     sizes, offs, tot = batch_layout(count, args.seed)
     keys_total = int(sum(int(m) for m in sizes))
@@ -858,6 +1146,8 @@ def run_batched(args):
     tuning = lp.lp_autotune_batched_u64(ctx, [int(m) for m in sizes])
     tune_s = time.perf_counter() - t0
     batch = lp.Batch(ctx, views, pivots, splits, seed=1)
+    lp.lp_fill_uniform_u64(buf, seed0)
+    pre_fp = segment_fingerprints(buf, offs, sizes)  # every step's input (untimed)
     for w in range(args.warmup):
         lp.lp_fill_uniform_u64(buf, seed0)
         batch.launch()
@@ -884,6 +1174,12 @@ def run_batched(args):
     torch.cuda.synchronize()
     wall_s = time.perf_counter() - wall0
     clk = clocks.stop()
+    # parity of the last timed launch's result, segment by segment
+    got = splits.cpu().tolist()
+    seg_ok = all(partition_holds(views[s_], got[s_], pivots[s_]) for s_ in range(count))
+    post_fp = segment_fingerprints(buf, offs, sizes)
+    lp.lp_fill_uniform_u64(buf, seed0)
+    counts_ok = all(count_le(views[s_], pivots[s_]) == got[s_] for s_ in range(count))
     # the same instances as separate plain launches (lp_partition_u64_async each)
     p_ms, p_launches = [], 0
     for k in range(max(1, min(args.steps, 3))):
@@ -897,6 +1193,14 @@ def run_batched(args):
         ev1.synchronize()
         p_ms.append(ev0.elapsed_time(ev1))
     same_splits = bool(torch.equal(splits, splits_plain))
+    parity = {"splits_equal_counts": counts_ok, "postcondition_every_segment": seg_ok,
+              "permutation_fingerprint_every_segment": pre_fp == post_fp,
+              "same_splits_as_plain_launches": same_splits,
+              "checked": "last timed launch: each segment's split vs the count of its keys "
+                         "<= its pivot, the postcondition in each segment, each segment's "
+                         "multiset fingerprint before and after; splits of the %d plain "
+                         "launches" % count}
+    parity["ok"] = counts_ok and seg_ok and pre_fp == post_fp and same_splits
     ms = sum(g_ms) / len(g_ms)
     keys_all, ms_all = whole_job(ws, keys_total, ms)
     value = keys_all / (ms_all / 1e3) / 1e9
@@ -904,6 +1208,7 @@ def run_batched(args):
     peak, peak_kind = measured_peaks()
     sk = sum(streamed) / len(streamed)
     achieved = 2 * 8 * sk / (ms / 1e3) / 1e9
+    traffic, traffic_why = profiled_traffic("batched", sk)
     result = {
         "metric": "batched partition keys/s (%d uint64 instances, sizes log-uniform "
                   "[2^8, 2^22])" % count,
@@ -920,7 +1225,7 @@ def run_batched(args):
                          % (8 * keys_total / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "batched_kernel<uint64_t> (one graph: set-up kernel + "
                                "persistent kernel)",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": 2 * 8 * sk,
@@ -930,6 +1235,7 @@ def run_batched(args):
                                   "calls": count, "gpu_launches": p_launches // len(p_ms),
                                   "speedup_of_batched": plain_ms / ms,
                                   "same_splits": same_splits},
+        "parity": parity,
         "streamed_keys_per_key": sk / keys_total,
         "gpu_launches": launches,
         "aux_bytes": ctx.aux_bytes,
@@ -937,6 +1243,8 @@ def run_batched(args):
     }
     if clk:
         result["clocks"] = clk
+    if traffic is None:
+        result["roofline"]["traffic_note"] = traffic_why
     if not args.no_e2e:
         host_in = torch.empty(tot, dtype=torch.int64, pin_memory=True)
         host_out = torch.empty(tot, dtype=torch.int64, pin_memory=True)
@@ -961,18 +1269,15 @@ def run_batched(args):
                          "path": "pinned host -> device, graph launch of the batch, "
                                  "device -> pinned host (keys and splits)"}
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, done, inst = cpu_oracle_batch(sizes, args.seed, 10.0)
+        v, done, inst = cpu_oracle_batch(sizes, args.seed, 3.0 if args.steps <= 5 else 10.0)
         result["cpu_baseline"] = {
             "value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
             "sample": "the first %d instances (%d keys), serial two-pointer partition, pivot "
                       "a seeded element of each" % (inst, done),
             "host_cores_available": os.cpu_count()}
     batch.close()
-    if rank == 0:
-        print(json.dumps(result))
     ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    return result
 
 
 # ---------------------------------------------------------------- serve
@@ -1016,6 +1321,44 @@ def run_serve(args):
     ws, rank, local = dist_env()
     init_dist(local, ws)
     from paper_2004_12532_gb300 import binding as lp
+    result = measure_serve(args, lp)
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def serve_parity(lp, reqs, cont, one, sample_every=7):
+    """Partition requests: the split of the continuous run equals that of the
+    same requests one at a time, and for every sample_every-th partition request
+    it equals the count of keys <= pivot of that request's keys, regenerated
+    from its seed as the server generates them (lp_fill_uniform_*)."""
+    import torch
+    same, counted, ok_count = True, 0, True
+    parts = [i for i, r in enumerate(reqs) if r.kind == lp.LP_REQ_PARTITION]
+    for j, i in enumerate(parts):
+        same = same and cont[i]["split"] == one[i]["split"]
+        if j % sample_every == 0:
+            r = reqs[i]
+            kd = torch.empty(r.n, dtype=torch.int64 if r.key_bits == 64 else torch.int32,
+                             device="cuda")
+            (lp.lp_fill_uniform_u64 if r.key_bits == 64 else lp.lp_fill_uniform_u32)(kd, r.seed)
+            ok_count = ok_count and count_le(kd, r.pivot) == cont[i]["split"]
+            counted += 1
+            del kd
+    return {"partition_splits_same_in_both_modes": same, "splits_equal_counts": ok_count,
+            "ok": same and ok_count,
+            "checked": "the first step's %d partition requests: continuous vs one at a time; "
+                       "%d of them against the count of their regenerated keys; sort "
+                       "results are checked by the test suite (alone and in a mix)" % (
+                           len(parts), counted)}
+
+
+def measure_serve(args, lp):
+    """The serving workload (Poisson arrivals at args.rate, args.requests per
+    step) against the same requests one at a time; returns its JSON object."""
+    import torch
+    ws, rank, local = dist_env()
     budget = int(args.budget_gib * (1 << 30))
     srv = lp.Server(local, budget_bytes=budget, max_slots=args.slots, seed=args.seed,
                     timing=True)
@@ -1033,6 +1376,8 @@ def run_serve(args):
     for k in range(args.steps):
         reqs = serve_requests(lp, args.requests, args.rate, seed0 + k)
         out = srv.run(reqs)
+        if k == 0:
+            first_out = out
         summ = latency_summary(reqs, out)
         summaries.append(summ)
         all_lat += [(c["done_s"] - c["arrival_s"]) * 1e3 for c in out]
@@ -1044,7 +1389,9 @@ def run_serve(args):
     s64_1, s32_1 = srv.streamed_keys()
     # the first step's requests again, one at a time through the plain calls
     reqs0 = serve_requests(lp, args.requests, args.rate, seed0)
-    base = latency_summary(reqs0, srv.run(reqs0, mode=lp.LP_SERVE_ONE_AT_A_TIME))
+    one = srv.run(reqs0, mode=lp.LP_SERVE_ONE_AT_A_TIME)
+    base = latency_summary(reqs0, one)
+    parity = serve_parity(lp, reqs0, first_out, one)
     ms = span_total / args.steps * 1e3
     keys_all, ms_all = whole_job(ws, keys_total / args.steps, ms)
     value = keys_all / (ms_all / 1e3) / 1e9
@@ -1071,8 +1418,11 @@ def run_serve(args):
                     "p99_ms": float(np.percentile(lat, 99)),
                     "per_step": summaries},
         "one_at_a_time": base,
+        "parity": parity,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
+                     "traffic_note": "mixed key widths and launch sizes; the batched "
+                                     "kernel's capture (batched object) covers the kernel",
                      "kernel": "batched_kernel (uint64 and uint32 launches of the engine "
                                "steps)", "peak_kind": peak_kind,
                      "algorithmic_bytes": b_bytes, "ms": b_ms},
@@ -1087,11 +1437,42 @@ def run_serve(args):
     }
     if clk:
         result["clocks"] = clk
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, keys, served = cpu_oracle_serve(args.seed, 2.0 if args.steps <= 5 else 5.0)
+        result["cpu_baseline"] = {
+            "value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": "%d requests of the same mix in stream order (%d keys), one at a time: "
+                      "serial two-pointer partition / serial quicksort, service time only"
+                      % (served, keys),
+            "host_cores_available": os.cpu_count()}
     srv.close()
-    if rank == 0:
-        print(json.dumps(result))
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    return result
+
+
+def cpu_oracle_serve(seed, budget_s):
+    """The oracle serving the request mix one request at a time on one host
+    core, for about budget_s seconds of service time; (Gkeys/s, keys, requests)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    sizes = inputs.log_uniform_sizes(4096, seed, 10, 26)
+    spent, keys, served = 0.0, 0, 0
+    for i, m in enumerate(sizes):
+        if spent > budget_s:
+            break
+        bits = 64 if rng.random() < 0.5 else 32
+        a = inputs.uniform_u64(int(m), seed + i) if bits == 64 else \
+            inputs.uniform_u32(int(m), seed + i)
+        sort = rng.random() < 0.3
+        pivot = inputs.quantile_pivot(int(rng.integers(1, 100)), 100, bits)
+        t0 = time.perf_counter()
+        if sort:
+            oracle.quicksort(a, i)
+        else:
+            oracle.partition(a, pivot)
+        spent += time.perf_counter() - t0
+        keys += int(m)
+        served += 1
+    return keys / spent / 1e9, keys, served
 
 
 def main():
