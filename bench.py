@@ -987,6 +987,8 @@ def measure_quicksort(args, lp):
     pms = sum(s_["partition_ms"] for s_ in stats) / len(stats)
     sk = sum(s_["sort_keys"] for s_ in stats) / len(stats)
     sms = sum(s_["sort_ms"] for s_ in stats) / len(stats)
+    tk = sum(s_["tail_keys"] for s_ in stats) / len(stats)
+    tms = sum(s_["tail_ms"] for s_ in stats) / len(stats)
     achieved = 2 * 8 * pk / (pms / 1e3) / 1e9
     traffic, why = profiled_traffic("quicksort", pk)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -997,11 +999,14 @@ def measure_quicksort(args, lp):
                 "algorithmic_bytes_per_step": 2 * 8 * pk, "ms_per_step": pms,
                 "sort_kernel": {"achieved": 2 * 8 * sk / (sms / 1e3) / 1e9 if sms else None,
                                 "ms_per_step": sms, "keys": sk},
-                # the whole sort: every key streamed by a partition level or sorted
-                # on chip is read and written once (2K bytes), over the step time
-                "whole_sort": {"algorithmic_bytes": 2 * 8 * (pk + sk), "ms": ms,
-                               "achieved": 2 * 8 * (pk + sk) / (ms / 1e3) / 1e9,
-                               "frac": 2 * 8 * (pk + sk) / (ms / 1e3) / 1e9 / peak}}
+                "tail_kernel": {"ms_per_step": tms, "streamed_keys": tk,
+                                "items": stats[-1]["tail_items"]},
+                # the whole sort: every key streamed by a partition (levels and tail)
+                # or sorted on chip is read and written once (2K bytes), over the
+                # step time
+                "whole_sort": {"algorithmic_bytes": 2 * 8 * (pk + tk + sk), "ms": ms,
+                               "achieved": 2 * 8 * (pk + tk + sk) / (ms / 1e3) / 1e9,
+                               "frac": 2 * 8 * (pk + tk + sk) / (ms / 1e3) / 1e9 / peak}}
     if traffic is None:
         roofline["traffic_note"] = why
     result = {
@@ -1018,7 +1023,7 @@ def measure_quicksort(args, lp):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": roofline,
         "levels": stats[-1]["levels"],
-        "partition_keys_per_key": pk / n,
+        "partition_keys_per_key": (pk + tk) / n,
         "gpu_launches": launches,
         "parity": parity,
         "sorted_last_step": sorted_ok,

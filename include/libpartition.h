@@ -215,14 +215,20 @@ lp_status lp_ctx_set_batch_tuning(lp_ctx *ctx, const lp_batch_tuning *tuning);
  * Quicksort") built on the partition.  Level-synchronous: every level
  * partitions all open subarrays (more than 4096 keys) at once through the
  * batched engine, each by [x <= p] with p the median of three keys at
- * positions drawn from `seed` and the subarray's place; a subarray where no
- * key exceeds p is partitioned again by [x < p] and the keys equal to p are
- * final (the paper is silent on pivots and duplicates).  Subarrays of at most
- * 4096 keys are sorted by one CTA each in shared memory.  The result is the
- * sorted array, whatever the seed; the seed only changes the work done.
- * Scratch: about 90 bytes per 4096 keys plus ~2.4 MB at most of per-segment
- * records, held by ctx.  Synchronises `stream` once or twice per level (the
- * host reads the list sizes) and before returning.  Errors: LP_ERR_INVALID_ARG
+ * positions drawn from `seed` and the subarray's place and level; a subarray
+ * where no key exceeds p is partitioned again by [x < p] and the keys equal to
+ * p are final (the paper is silent on pivots and duplicates).  Subarrays of at
+ * most 4096 keys are sorted by one CTA each in shared memory (a bucket sort on
+ * the subarray's key range, or a merge sort when the keys bunch).  Once a
+ * level holds at most 4096 open subarrays, fewer than a quarter of the most
+ * any level held, none of more than 131072 keys, each of them is sorted
+ * completely by one CTA (Partial
+ * Partition Steps by its warps, on-chip partitions, the shared-memory sort)
+ * in one launch, instead of a level at a time.  The result
+ * is the sorted array, whatever the seed; the seed only changes the work done.
+ * Scratch: about 100 bytes per 4096 keys plus ~2.4 MB at most of per-segment
+ * records, held by ctx.  Synchronises `stream` once per level (the host reads
+ * the list sizes) and before returning.  Errors: LP_ERR_INVALID_ARG
  * (null or misaligned array), LP_ERR_OOM, LP_ERR_TIMEOUT (a bounded device
  * wait gave up), LP_ERR_CUDA. */
 lp_status lp_quicksort_u64(lp_ctx *ctx, uint64_t *keys, uint64_t n, uint64_t seed,
@@ -240,14 +246,18 @@ lp_status lp_quicksort_ex_u32(lp_ctx *ctx, uint32_t *keys, uint64_t n, uint64_t 
 /* What the last lp_quicksort_* on ctx did.  Keys "streamed" are read once and
  * written once by a kernel: the algorithmic traffic is 2 x key bytes x keys.
  * The times are device times (CUDA events) and are set only when timing is on
- * (lp_ctx_set_timing); timing adds one stream synchronisation per level. */
+ * (lp_ctx_set_timing). */
 typedef struct {
   uint32_t levels;          /* partition levels (each one batched launch or more) */
   uint32_t timed;           /* 1 if the two times below were measured */
   uint64_t partition_keys;  /* keys streamed by the batched partitions, all levels */
   uint64_t sort_keys;       /* keys sorted in shared memory */
   float partition_ms;       /* device time of the partition levels */
-  float sort_ms;            /* device time of the shared-memory sorts */
+  float sort_ms;            /* device time of the levels' shared-memory sorts */
+  uint32_t tail_items;      /* open subarrays the tail kernel sorted (0: none) */
+  float tail_ms;            /* device time of the tail kernel */
+  uint64_t tail_keys;       /* keys streamed by the tail kernel's partitions (its
+                               shared-memory sorts are in sort_keys) */
 } lp_sort_stats;
 lp_status lp_ctx_sort_stats(const lp_ctx *ctx, lp_sort_stats *out);
 

@@ -45,7 +45,8 @@ class lp_batch_tuning(C.Structure):
 
 class lp_sort_stats(C.Structure):
     _fields_ = [("levels", C.c_uint32), ("timed", C.c_uint32), ("partition_keys", C.c_uint64),
-                ("sort_keys", C.c_uint64), ("partition_ms", C.c_float), ("sort_ms", C.c_float)]
+                ("sort_keys", C.c_uint64), ("partition_ms", C.c_float), ("sort_ms", C.c_float),
+                ("tail_items", C.c_uint32), ("tail_ms", C.c_float), ("tail_keys", C.c_uint64)]
 
 
 class lp_server_config(C.Structure):

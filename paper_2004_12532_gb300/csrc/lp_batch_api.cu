@@ -346,6 +346,9 @@ lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, uint32_t
   c->sort_stats.sort_keys = ss.sort_keys;
   c->sort_stats.partition_ms = ss.partition_ms;
   c->sort_stats.sort_ms = ss.sort_ms;
+  c->sort_stats.tail_items = ss.tail_items;
+  c->sort_stats.tail_ms = ss.tail_ms;
+  c->sort_stats.tail_keys = ss.tail_keys;
   e = cudaMemcpyAsync(c->h_pinned, c->task.status, 4, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "read status");

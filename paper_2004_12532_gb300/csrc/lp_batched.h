@@ -96,10 +96,13 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
 // (three events, or null) times the partition levels and the shared-memory
 // sorts.
 struct SortStats {
-  uint32_t levels;
-  uint64_t partition_keys;  // keys streamed by the batched partitions (all levels)
-  uint64_t sort_keys;       // keys sorted in shared memory
+  uint32_t levels;          // level-synchronous levels
+  uint64_t partition_keys;  // keys streamed by their batched partitions
+  uint64_t sort_keys;       // keys sorted in shared memory (levels and tail)
   float partition_ms, sort_ms;
+  uint32_t tail_items;      // subarrays the tail kernel finished (0: no tail)
+  uint64_t tail_keys;       // keys streamed by the tail kernel's partitions
+  float tail_ms;            // its device time
 };
 
 size_t quicksort_scratch_bytes(uint64_t n);

@@ -6,36 +6,12 @@
 #include <stdint.h>
 
 #include "lp_qs.cuh"
+#include "lp_qs_pivot.cuh"
 #include "lp_qs_sort.cuh"
 
 namespace lp {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T qs_ld(const T* p) {
-  if constexpr (sizeof(T) == 8) return (T)__ldcg(reinterpret_cast<const unsigned long long*>(p));
-  else return (T)__ldcg(reinterpret_cast<const unsigned int*>(p));
-}
-
-// The median of NS keys at seeded positions of keys[lo, lo + n): all loads
-// first, then an insertion sort in registers (fully unrolled).
-template <uint32_t NS, typename T>
-__device__ __forceinline__ T qs_median(const T* keys, uint64_t lo, uint64_t n, uint64_t h) {
-  T v[NS];
-#pragma unroll
-  for (uint32_t j = 0; j < NS; j++) v[j] = qs_ld(&keys[lo + range_of(sm_stream(h, j), n)]);
-#pragma unroll
-  for (uint32_t j = 1; j < NS; j++) {
-#pragma unroll
-    for (uint32_t r = j; r > 0; r--) {
-      const T a = v[r - 1] < v[r] ? v[r - 1] : v[r], b = v[r - 1] < v[r] ? v[r] : v[r - 1];
-      v[r - 1] = a;
-      v[r] = b;
-    }
-  }
-  return v[NS / 2];
-}
 
 // Segment records of every job slice: blockIdx.y = job, x = item.
 template <typename T>
@@ -45,7 +21,7 @@ __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
   if (i >= J.count) return;
   const QsItem q = J.items[i];
   T* keys = static_cast<T*>(J.keys);
-  const uint64_t h = sm_stream(J.seed + J.level, q.lo ^ (q.n << 32));
+  const uint64_t h = qs_item_hash(J.seed, J.level, q.lo, q.n);
   SegDesc d = {};
   d.keys = keys + q.lo;
   d.n = q.n;
@@ -62,11 +38,12 @@ __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
 
 __device__ __forceinline__ void qs_push(const QsJob& J, uint64_t lo, uint64_t n) {
   if (n <= 1) return;  // a single key is in place
-  if (n <= kQsCut) {
-    J.small[atomicAdd(&J.lc->small, 1u)] = QsSmall{lo, n};
+  if (n <= (J.local_cut ? (uint64_t)J.local_cut : kQsCut)) {
+    J.small[atomicAdd(&J.lc->small, 1u)] = QsSmall{lo, n, J.level + 1, 0u};
     atomicAdd(J.sort_keys, (unsigned long long)n);
   } else {
     J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{lo, n, 0, 0};
+    atomicMax(&J.lc->max_next, n < 0xffffffffull ? (uint32_t)n : 0xffffffffu);
   }
 }
 
@@ -85,7 +62,10 @@ __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const ui
   }
   if (t == q.n) {  // no successor: split off the keys equal to the pivot next level
     const uint64_t p = segs[J.seg_base + i].pivot;
-    if (p != 0) J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{q.lo, q.n, p, 1};
+    if (p != 0) {
+      J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{q.lo, q.n, p, 1};
+      atomicMax(&J.lc->max_next, q.n < 0xffffffffull ? (uint32_t)q.n : 0xffffffffu);
+    }
     return;
   }
   qs_push(J, q.lo, t);
@@ -93,7 +73,7 @@ __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const ui
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kQsSortThreads, 4) qs_small_sort_kernel(const QsJob* jobs) {
+__global__ void __launch_bounds__(kQsSortThreads, 3) qs_small_sort_kernel(const QsJob* jobs) {
   extern __shared__ __align__(16) unsigned char qs_smem[];
   const QsJob& J = jobs[blockIdx.y];
   const uint32_t cnt = *reinterpret_cast<volatile uint32_t*>(&J.lc->small);

@@ -34,10 +34,14 @@ struct QsItem {
 };
 struct QsSmall {
   uint64_t lo, n;
+  uint32_t level;  // the subarray's level (names its pivot when it is partitioned further)
+  uint32_t pad;
 };
 // per-job list sizes of the current level (reset every level), in device memory
 struct QsLevelCounts {
   uint32_t next, small;
+  uint32_t max_next;  // keys of the largest item of the next list (saturated at 2^32 - 1)
+  uint32_t pad;
 };
 
 // One slice of one job's list in one launch.
@@ -53,6 +57,8 @@ struct QsJob {
   uint32_t count;                  // items in this slice
   uint32_t seg_base;               // index of the slice's first segment record
   uint32_t samples;                // pivot: median of this many seeded keys (3 or 15; 0: 3)
+  uint32_t local_cut;              // children of at most this many keys go to the small
+                                   // list (0: kQsCut, the shared-memory sort's size)
 };
 
 // Segment records of every job in `jobs` (grid.y = jobs, x covers the
@@ -75,5 +81,21 @@ cudaError_t launch_qs_small_sort(const QsJob* jobs, uint32_t njobs, uint32_t cta
 
 // Sets the shared-memory attribute of the sort kernels (once per device).
 cudaError_t qs_prepare();
+
+// The tail of a sort (lp_qs_local.cu): every item list[0..count) of level
+// `level` (open subarrays, normal or equal-key) is sorted completely by one
+// CTA, depth first -- Partial Partition Steps by its warps, on-chip
+// partitions, then the shared-memory sort of pieces of at most kQsCut keys --
+// with no grid-wide barrier.  Pivots as in the levels (qs_item_hash).
+// acc[0] += keys streamed by its partitions, acc[1] += keys it sorted in
+// shared memory, acc[3] / acc[4] += the CTAs' device time (ns, summed over
+// CTAs) in sorts / in partitions; acc[2] is its fetch counter.  `grid`: CTAs
+// (at most qs_local_grid).
+template <typename T>
+cudaError_t launch_qs_local(T* keys, const QsItem* list, uint32_t count, uint32_t level,
+                            uint64_t seed, uint32_t samples, unsigned long long* acc,
+                            uint32_t* status, uint32_t grid, cudaStream_t st);
+template <typename T>
+cudaError_t qs_local_grid(int device, uint32_t* grid);
 
 }  // namespace lp

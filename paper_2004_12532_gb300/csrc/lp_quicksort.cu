@@ -24,6 +24,14 @@ namespace {
 
 constexpr uint32_t kSlice = 16384;  // segments per batched launch, at most
 constexpr uint32_t kMaxSortLevels = 4096;
+// The tail: once a level holds at most kTailItems open subarrays, fewer than
+// 1/kTailDrop of the most any level held, none of more than kTailMaxKeys keys,
+// each of them is sorted by one CTA in one launch (lp_qs_local.cu) instead of
+// a level at a time -- the last levels hold few keys and would each cost a
+// level's fixed overhead.
+constexpr uint64_t kTailItems = 4096;
+constexpr uint64_t kTailDrop = 4;
+constexpr uint64_t kTailMaxKeys = 131072;
 
 struct QsLayout {
   QsItem* lists[2];
@@ -32,7 +40,8 @@ struct QsLayout {
   uint64_t* splits;
   QsJob* jobs;                      // one record per slice
   QsLevelCounts* lc;
-  unsigned long long* acc;          // [0] keys streamed by partitions, [1] keys sorted
+  unsigned long long* acc;          // [0] keys streamed by partitions, [1] keys sorted,
+                                    // [2..6] the tail kernel's tallies (launch_qs_local)
   void* batch;
   uint64_t maxseg;
   uint32_t slice, max_slices;
@@ -58,7 +67,7 @@ QsLayout qs_layout(void* base, uint64_t n) {
   L.splits = reinterpret_cast<uint64_t*>(take((size_t)L.slice * 8));
   L.jobs = reinterpret_cast<QsJob*>(take((size_t)L.max_slices * sizeof(QsJob)));
   L.lc = reinterpret_cast<QsLevelCounts*>(take(sizeof(QsLevelCounts)));
-  L.acc = reinterpret_cast<unsigned long long*>(take(16));
+  L.acc = reinterpret_cast<unsigned long long*>(take(64));
   L.batch = take(batch_scratch_bytes(L.slice));
   L.bytes = off;
   return L;
@@ -84,7 +93,11 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
   QsJob* hjobs = static_cast<QsJob*>(staging);
   unsigned char* hback = static_cast<unsigned char*>(staging) + L.max_slices * sizeof(QsJob);
   const uint64_t batch_seed = sm_stream(seed, 0x51);
-  cudaError_t e = cudaMemsetAsync(L.acc, 0, 16, st);
+  int dev = 0;
+  uint32_t tail_grid = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = qs_local_grid<T>(dev, &tail_grid);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.acc, 0, 64, st);
   if (e != cudaSuccess) return e;
   // the first level: the whole array as one item, or as the only small subarray
   uint64_t open = 0;
@@ -93,11 +106,11 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
     e = cudaMemcpyAsync(L.lists[0], &whole, sizeof(whole), cudaMemcpyHostToDevice, st);
     open = 1;
   } else {
-    const QsSmall whole{0, n};
+    const QsSmall whole{0, n, 0u, 0u};
     e = cudaMemcpyAsync(L.small, &whole, sizeof(whole), cudaMemcpyHostToDevice, st);
   }
   if (e != cudaSuccess) return e;
-  const QsLevelCounts first{0, n > kQsCut ? 0u : 1u};
+  const QsLevelCounts first{0, n > kQsCut ? 0u : 1u, 0u, 0u};
   e = cudaMemcpyAsync(L.lc, &first, sizeof(first), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   auto mark = [&](int k) -> cudaError_t { return ev ? cudaEventRecord(ev[k], st) : cudaSuccess; };
@@ -106,6 +119,7 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
     if (ev && cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess) *acc += ms;
   };
   uint32_t cur = 0, levels = 0;
+  uint64_t peak_open = open;
   for (;;) {
     // one record per slice of the level's list (one record, of no items,
     // for the small-only first level: the small sort reads its lists)
@@ -125,6 +139,7 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
       J.count = (uint32_t)(open > o ? (open - o < L.slice ? open - o : L.slice) : 0);
       J.seg_base = 0;
       J.samples = samples;
+      J.local_cut = 0;
     }
     if (levels > 0) e = cudaMemsetAsync(L.lc, 0, sizeof(QsLevelCounts), st);
     if (e == cudaSuccess)
@@ -157,17 +172,33 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
     if (nslices == 0) break;  // the small-only first level is done
     levels++;
     open = reinterpret_cast<const QsLevelCounts*>(hback)->next;
+    const uint64_t max_item = reinterpret_cast<const QsLevelCounts*>(hback)->max_next;
     cur ^= 1;
     if (open == 0) break;
     if (levels > kMaxSortLevels) return cudaErrorUnknown;  // sizes shrink every level
+    if (open > peak_open) peak_open = open;
+    if (open <= kTailItems && open * kTailDrop < peak_open &&
+        max_item <= kTailMaxKeys) {  // the tail, in one launch
+      if ((e = mark(1)) != cudaSuccess) return e;
+      e = launch_qs_local<T>(keys, L.lists[cur], (uint32_t)open, levels, seed, samples,
+                             L.acc + 2, status, tail_grid, st);
+      if (e != cudaSuccess) return e;
+      cfg.launches += 2;  // counter reset + kernel
+      if ((e = mark(2)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+      elapsed(1, 2, &stats->tail_ms);
+      stats->tail_items = (uint32_t)open;
+      break;
+    }
   }
-  e = cudaMemcpyAsync(hback, L.acc, 16, cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(hback, L.acc, 56, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e;
   const unsigned long long* acc = reinterpret_cast<const unsigned long long*>(hback);
   stats->levels = levels;
   stats->partition_keys = acc[0];
-  stats->sort_keys = acc[1] + (n <= kQsCut ? n : 0);
+  stats->sort_keys = acc[1] + acc[3] + (n <= kQsCut ? n : 0);
+  stats->tail_keys = acc[2];
   return cudaGetLastError();
 }
 

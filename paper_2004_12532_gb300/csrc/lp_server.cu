@@ -61,7 +61,7 @@ __global__ void qs_begin_kernel(const QsBegin* b, uint32_t count) {
   QsLevelCounts c{0u, 0u};
   if (x.mode == 1) x.list0[0] = QsItem{0, x.n, 0, 0};
   if (x.mode == 2) {
-    x.small[0] = QsSmall{0, x.n};
+    x.small[0] = QsSmall{0, x.n, 0u, 0u};
     c.small = 1u;
   }
   *x.lc = c;
@@ -393,6 +393,7 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
     J.count = (uint32_t)q.open;
     J.seg_base = nsegs[k];
     J.samples = lp::kQsSamplesMax;  // median-of-15 pivots: fewer levels, lower latency
+    J.local_cut = 0;                // small children: the shared-memory sort of each step
     nsegs[k] += (uint32_t)q.open;
     if (q.open > max_open[k]) max_open[k] = q.open;
     const uint64_t sb = q.open ? 2 * q.open : 1;

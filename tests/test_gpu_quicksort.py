@@ -67,7 +67,11 @@ def run_and_compare(ctx, host, seed=5):
     assert np.array_equal(out, ref)
 
 
-SIZES = [0, 1, 2, 3, 17, 4095, 4096, 4097, 8191, 12289, 65536 + 7, 1 << 20, (1 << 21) + 333]
+# around the shared-memory sort (4096 keys), one CTA's on-chip partition
+# (about 12K uint64 keys), the finishing kernel's cut (65536 keys: larger
+# subarrays go through the level-synchronous levels first), several levels
+SIZES = [0, 1, 2, 3, 17, 4095, 4096, 4097, 8191, 12289, 40000, 65535, 65536, 65537,
+         65536 + 7, 131073, 1 << 20, (1 << 21) + 333]
 
 
 @pytest.mark.parametrize("n", SIZES)
@@ -76,13 +80,13 @@ def test_uniform_u64_sizes(ctx, n):
 
 
 @pytest.mark.parametrize("kind", ["sorted", "reverse", "dup16", "equal", "zeros", "max", "two"])
-@pytest.mark.parametrize("n", [5000, 300000])
+@pytest.mark.parametrize("n", [5000, 50001, 300000])
 def test_patterns_u64(ctx, kind, n):
     run_and_compare(ctx, make(kind, n, 7 + n))
 
 
 @pytest.mark.parametrize("kind", ["uniform", "dup16"])
-@pytest.mark.parametrize("n", [1, 4096, 4097, 100003, 1 << 20, 1 << 25])
+@pytest.mark.parametrize("n", [1, 4096, 4097, 30001, 65536, 65537, 100003, 1 << 20, 1 << 25])
 def test_u32(ctx, kind, n):
     # 2^25 keys: the first levels leave open ranges that several CTAs finish
     # on chip at once (the batched engine's multi-CTA finish for 4-byte keys)
