@@ -49,7 +49,6 @@ struct LowArgs {
   uint64_t* v;                     // nb prefix counters
   uint64_t nb_cap;                 // counters the scratch holds
   unsigned long long* cta;         // one word per CTA
-  unsigned long long* total;       // predecessor count of the range
   uint64_t* split;                 // if set: the split (count) is written here
   unsigned long long* tl;          // device timestamps: start, then the end of each phase
   int prefix_only;                 // values kept in key order: stop after the prefix phase
@@ -365,10 +364,14 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     unsigned long long c =
         count_span(A, 0, n, gtid, gstride, [&](T x) { return x <= pivot; });
     c = cta_sum(c, red);
-    if (tid == 0) atomicAdd(a.total, c);
+    if (tid == 0) __stcg(&a.cta[blockIdx.x], c);
   }
   if (!grid_barrier(S.bar, gridDim.x, &flag)) { fail(); return; }
-  const uint64_t cnt = __ldcg(a.total);
+  // every CTA adds up all CTAs' counts (the words are rewritten only after
+  // the next grid barrier)
+  unsigned long long cpart = 0;
+  for (uint32_t c2 = tid; c2 < gridDim.x; c2 += kLT) cpart += __ldcg(&a.cta[c2]);
+  const uint64_t cnt = cta_sum(cpart, red);
   if (leader && a.split) *a.split = cnt;
   stamp(1);
   if (n < 2) return;
@@ -700,7 +703,6 @@ cudaError_t launch_lowspace_impl(T* keys, uint64_t* vals, uint64_t lo, uint64_t 
   p += ((nb + 1) * 8 + 255) / 256 * 256;
   a.cta = reinterpret_cast<unsigned long long*>(p);
   p += ((size_t)cfg.grid * 8 + 255) / 256 * 256;
-  a.total = reinterpret_cast<unsigned long long*>(p);
   a.tl = reinterpret_cast<unsigned long long*>(p + 256);
   a.split = split;
   a.prefix_only = prefix_only;
@@ -721,10 +723,11 @@ cudaError_t launch_lowspace_impl(T* keys, uint64_t* vals, uint64_t lo, uint64_t 
   const uint64_t cap = (uint64_t)grid * Coop<T, KV>::Keys;
   a.base_keys = base_keys < cap ? base_keys : cap;
   if (a.base_keys < 5 * B) a.base_keys = 0;  // the paper's base case decides
-  e = cudaMemsetAsync(a.total, 0, 8, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.tl, 0, 8 * kLowPhases, st);
-  if (e != cudaSuccess) return e;
-  if (cfg.phase_stamps) *cfg.phase_stamps = a.tl;
+  if (cfg.phase_stamps) {  // the caller reads the phase timestamps: no stale ones
+    e = cudaMemsetAsync(a.tl, 0, 8 * kLowPhases, st);
+    if (e != cudaSuccess) return e;
+    *cfg.phase_stamps = a.tl;
+  }
   e = launch_cooperative(lowspace_kernel<T, KV, IMP>, grid, kLT, smem, st, keys, vals, a, S);
   cfg.launches++;
   return e;
