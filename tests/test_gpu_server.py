@@ -193,3 +193,41 @@ def test_open_loop_run_and_one_at_a_time():
     assert st["completed"] == 2 * len(reqs)
     assert sum(srv.streamed_keys()) > 0
     srv.close()
+
+
+def device_keys(n, bits, seed):
+    """A request's keys as the server generates them from its seed (src=None):
+    lp_fill_uniform_*, copied to the host."""
+    d = torch.empty(n, dtype=torch.int64 if bits == 64 else torch.int32, device="cuda")
+    (lp.lp_fill_uniform_u64 if bits == 64 else lp.lp_fill_uniform_u32)(d, seed)
+    return d.cpu().numpy().view(np.uint64 if bits == 64 else np.uint32)
+
+
+def test_large_requests_same_alone_and_in_mix():
+    """The serving workload's large requests (2^24 .. 2^26 keys, both widths):
+    multi-level Smoothed Striding steps and multi-CTA finishes for partitions,
+    deep quicksort levels for sorts, all inside one mix with small requests.
+    Each result equals, byte for byte, the same request run alone, and the
+    oracle's result (a partition's split and sides; a sort's bytes)."""
+    big = [(P, 64, 1 << 26), (S, 64, 1 << 24), (P, 32, (1 << 25) + 3), (S, 32, 1 << 26),
+           (P, 64, (1 << 24) + 1), (S, 64, (1 << 25) + 5)]
+    small = [(P, 32, 5000), (S, 64, 70001), (P, 64, 300000), (S, 32, 4097)]
+    reqs = []
+    for i, (kind, bits, n) in enumerate(big + small):
+        q = (1, 100) if i % 3 == 0 else ((1, 2) if i % 3 == 1 else (99, 100))
+        reqs.append((kind, bits, n, inputs.quantile_pivot(q[0], q[1], bits), 0xB16 + i))
+    mix = lp.Server(budget_bytes=4 << 30, max_slots=16, keep_results=True, seed=11)
+    ids = [mix.submit(kind, bits, n, pivot=pivot, seed=seed)
+           for kind, bits, n, pivot, seed in reqs]
+    drain(mix, len(reqs))
+    in_mix = [mix.fetch(i, r[2], r[1]) for i, r in zip(ids, reqs)]
+    assert mix.stats()["peak_bytes"] <= 4 << 30
+    mix.close()
+    for k, (kind, bits, n, pivot, seed) in enumerate(reqs):
+        alone = lp.Server(budget_bytes=1 << 30, max_slots=2, keep_results=True, seed=11)
+        i = alone.submit(kind, bits, n, pivot=pivot, seed=seed)
+        c = drain(alone, 1)[0]
+        out = alone.fetch(i, n, bits)
+        alone.close()
+        assert np.array_equal(out, in_mix[k]), (k, kind, bits, n)
+        check_result(kind, bits, n, pivot, device_keys(n, bits, seed), out, c["split"])
