@@ -191,8 +191,13 @@ lp_status host_partition(lp_ctx* c, T* host, uint64_t n, T pivot, uint64_t seed,
       return bail(lp_fail(c, LP_ERR_INTERNAL, "host partition plan stalled"));
     if ((e = cudaEventSynchronize(H.ev_part[j])) != cudaSuccess)
       return bail(lp_cuda_fail(c, e, "partition of a chunk"));
+    // a chunk whose partition failed on the device, or whose split cannot be
+    // one, plans no copy back: stop before the caller's array is written from it
     status |= (uint32_t)(H.h_slots[2 * j + 1] & 0xffffffffu);
-    plan.partitioned(H.h_slots[2 * j]);
+    if (status & kStatTimeout) return bail(lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out"));
+    if (status) return bail(lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed"));
+    if (!plan.partitioned(H.h_slots[2 * j]))
+      return bail(lp_fail(c, LP_ERR_INTERNAL, "a chunk's split exceeds its length"));
     pieces.clear();
     plan.take_pieces(pieces);
     if (!pieces.empty() && (e = cudaStreamWaitEvent(H.s_down, H.ev_part[j], 0)) != cudaSuccess)

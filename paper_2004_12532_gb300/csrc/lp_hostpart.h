@@ -77,8 +77,12 @@ class HostChunkPlan {
     return k;
   }
   // The next upload (in upload order) was partitioned on the device with p
-  // predecessors; its upload is complete.
-  void partitioned(uint64_t p) {
+  // predecessors; its upload is complete.  Returns false, changing nothing,
+  // when there is no such upload or p exceeds the chunk's length (never a
+  // valid split: no copy may be planned from it).
+  bool partitioned(uint64_t p) {
+    if (processed_ >= order_.size()) return false;
+    if (p > chunk_len(order_[processed_])) return false;
     const uint32_t q = processed_++;
     const uint32_t k = order_[q];
     const uint64_t len = chunk_len(k), s = len - p, d0 = chunk_begin(k);
@@ -94,6 +98,7 @@ class HostChunkPlan {
     } else if (d0 < bdone_) {
       bdone_ = d0;
     }
+    return true;
   }
   // Appends the copies that became legal: host positions in [0, fdone) or
   // [bdone, n) have reached the device.

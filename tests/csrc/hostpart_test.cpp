@@ -41,7 +41,7 @@ static bool run(std::vector<uint64_t>& host, uint64_t pivot, uint64_t C, uint32_
       std::copy(host.begin() + b, host.begin() + b + len, dev.begin() + b);  // the upload lands
       const auto mid = std::stable_partition(dev.begin() + b, dev.begin() + b + len,
                                              [&](uint64_t x) { return x <= pivot; });
-      plan.partitioned((uint64_t)(mid - (dev.begin() + b)));
+      if (!plan.partitioned((uint64_t)(mid - (dev.begin() + b)))) return false;
     } else if (plan.processed() < plan.needed_for_next()) {
       return false;  // nothing in flight, yet the next choice waits for a count
     }
@@ -101,6 +101,28 @@ int main(int argc, char** argv) {
       for (uint64_t i = 0; i < n; i++) in[i] = ((i / (1 + C / 2)) & 1) ? 999 : 0, pivot = 500;
     if (kind == 6) for (uint64_t i = 0; i < n; i++) in[i] = (i * 7919) % 1000;
     bad |= check(in, pivot, C, lag, "random");
+  }
+  // a split larger than its chunk is refused and plans nothing; the plan then
+  // accepts the chunk's real split
+  if (!bad) {
+    HostChunkPlan plan;
+    plan.init(1000, 300, 2);
+    const uint32_t k = plan.next_upload();
+    const uint64_t len = plan.chunk_len(k);
+    std::vector<HostPiece> pieces;
+    if (plan.partitioned(len + 1) || plan.processed() != 0) {
+      printf("FAIL: a split above the chunk length was accepted\n");
+      bad = 1;
+    }
+    plan.take_pieces(pieces);
+    if (!bad && !pieces.empty()) {
+      printf("FAIL: copies planned from a refused split\n");
+      bad = 1;
+    }
+    if (!bad && (!plan.partitioned(len / 2) || plan.processed() != 1)) {
+      printf("FAIL: a valid split after a refused one\n");
+      bad = 1;
+    }
   }
   if (!bad) printf("OK\n");
   return bad;
