@@ -294,7 +294,9 @@ lp_status lp_batch_round_stats(lp_batch *batch, cudaStream_t stream, lp_batch_ro
  * the shared-memory sorts of all those sorts; requests that arrive meanwhile
  * join the next step.  A partition finishes in the step it joins, a sort after
  * as many steps as its quicksort has levels (pivots: the median of 15 seeded
- * keys, as lp_quicksort_ex_* with 15, for fewer levels).  Each result is the
+ * keys, as lp_quicksort_ex_* with 15, for fewer levels), or sooner: once its
+ * open subarrays are few and small (the quicksort's tail rule), the next step
+ * sorts each of them completely, one CTA per subarray.  Each result is the
  * same whatever the request was batched with (a partition's offsets X follow
  * from the engine seed and the request seed only; a sort's result is the
  * sorted array).

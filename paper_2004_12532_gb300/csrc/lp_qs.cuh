@@ -82,6 +82,20 @@ cudaError_t launch_qs_small_sort(const QsJob* jobs, uint32_t njobs, uint32_t cta
 // Sets the shared-memory attribute of the sort kernels (once per device).
 cudaError_t qs_prepare();
 
+// The tail: once a level holds at most kQsTailItems open subarrays, fewer than
+// 1/kQsTailDrop of the most any level of the sort held, none of more than
+// kQsTailMaxKeys keys, each of them is sorted by one CTA in one launch
+// (launch_qs_local) instead of a level at a time -- the last levels hold few
+// keys and would each cost a level's fixed overhead (or, in the serving
+// engine, an engine step).
+constexpr uint64_t kQsTailItems = 4096;
+constexpr uint64_t kQsTailDrop = 4;
+constexpr uint64_t kQsTailMaxKeys = 131072;
+inline bool qs_is_tail(uint64_t open, uint64_t peak_open, uint64_t max_item) {
+  return open > 0 && open <= kQsTailItems && open * kQsTailDrop < peak_open &&
+         max_item <= kQsTailMaxKeys;
+}
+
 // The tail of a sort (lp_qs_local.cu): every item list[0..count) of level
 // `level` (open subarrays, normal or equal-key) is sorted completely by one
 // CTA, depth first -- Partial Partition Steps by its warps, on-chip

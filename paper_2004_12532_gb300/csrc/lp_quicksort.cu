@@ -24,14 +24,7 @@ namespace {
 
 constexpr uint32_t kSlice = 16384;  // segments per batched launch, at most
 constexpr uint32_t kMaxSortLevels = 4096;
-// The tail: once a level holds at most kTailItems open subarrays, fewer than
-// 1/kTailDrop of the most any level held, none of more than kTailMaxKeys keys,
-// each of them is sorted by one CTA in one launch (lp_qs_local.cu) instead of
-// a level at a time -- the last levels hold few keys and would each cost a
-// level's fixed overhead.
-constexpr uint64_t kTailItems = 4096;
-constexpr uint64_t kTailDrop = 4;
-constexpr uint64_t kTailMaxKeys = 131072;
+
 
 struct QsLayout {
   QsItem* lists[2];
@@ -177,8 +170,7 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
     if (open == 0) break;
     if (levels > kMaxSortLevels) return cudaErrorUnknown;  // sizes shrink every level
     if (open > peak_open) peak_open = open;
-    if (open <= kTailItems && open * kTailDrop < peak_open &&
-        max_item <= kTailMaxKeys) {  // the tail, in one launch
+    if (qs_is_tail(open, peak_open, max_item)) {  // the tail, in one launch
       if ((e = mark(1)) != cudaSuccess) return e;
       e = launch_qs_local<T>(keys, L.lists[cur], (uint32_t)open, levels, seed, samples,
                              L.acc + 2, status, tail_grid, st);

@@ -8,6 +8,10 @@
 // a step runs join the next step; a partition finishes in the step it joins,
 // a sort after as many steps as its quicksort has levels.
 //
+// A sort whose open subarrays are few and small (lp::qs_is_tail) finishes in
+// its next step instead: one tail launch sorts each of them completely, one
+// CTA per subarray.
+//
 // A request's result does not depend on what it was batched with: every
 // segment's offsets X follow from the engine seed and the segment's own salt
 // (the request seed, or a hash of the sort subarray), and the batched kernel
@@ -81,6 +85,8 @@ struct Req {
   QsSmall* small = nullptr;
   uint32_t cur = 0, level = 0, slot = 0;
   uint64_t open = 0;
+  uint64_t peak_open = 0;      // most open items any level of the sort held
+  uint64_t max_next = 0;       // keys of its largest open item
   // result
   uint64_t split = 0;
   double admit_s = 0, done_s = 0;
@@ -132,6 +138,8 @@ struct lp_server {
   bool timed[2] = {false, false};
   QsBegin* d_begin = nullptr;
   uint32_t* d_ctl = nullptr;           // grid barrier (2 words), status
+  unsigned long long* d_tail = nullptr;  // the tail kernels' tallies, 8 words per width
+  uint32_t tail_grid[2] = {0, 0};        // CTAs of the tail kernel, per width
   // pinned staging
   unsigned char* h_stage = nullptr;
   size_t stage_bytes = 0;
@@ -169,7 +177,7 @@ size_t engine_bytes(uint32_t C, uint32_t slots) {
   }
   b += lp::Arena::rounded((size_t)slots * sizeof(QsLevelCounts)) +
        lp::Arena::rounded((size_t)slots * 8) + 256 +
-       lp::Arena::rounded((size_t)slots * sizeof(QsBegin)) + 256;
+       lp::Arena::rounded((size_t)slots * sizeof(QsBegin)) + 256 + 256;
   return b;
 }
 
@@ -317,6 +325,8 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
         q.lists[1] = reinterpret_cast<QsItem*>(p + lp::Arena::rounded(m * sizeof(QsItem)));
         q.small = reinterpret_cast<QsSmall*>(p + 2 * lp::Arena::rounded(m * sizeof(QsItem)));
         q.open = 1;
+        q.peak_open = 1;
+        q.max_next = q.r.n;
       } else {
         q.small = reinterpret_cast<QsSmall*>(p);
         q.open = 0;
@@ -361,7 +371,7 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
   Stage S = stage_layout(s->h_stage, slots);
   uint32_t nparts[2] = {0, 0}, njobs[2] = {0, 0}, nsegs[2] = {0, 0}, nbegin = 0;
   uint64_t max_open[2] = {0, 0}, max_small[2] = {0, 0};
-  std::vector<uint64_t> part_ids[2], job_ids[2];
+  std::vector<uint64_t> part_ids[2], job_ids[2], tail_ids[2];
   for (uint64_t id : s->active) {  // partitions first: their records start each table
     Req& q = s->reqs[id];
     if (q.r.kind != LP_REQ_PARTITION) continue;
@@ -380,6 +390,10 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
     Req& q = s->reqs[id];
     if (q.r.kind != LP_REQ_SORT) continue;
     const int k = q.r.key_bits == 64 ? 0 : 1;
+    if (!q.fresh && lp::qs_is_tail(q.open, q.peak_open, q.max_next)) {
+      tail_ids[k].push_back(id);  // the rest of the sort in this step, one CTA per item
+      continue;
+    }
     if (nsegs[k] + q.open > C) continue;  // the whole level or nothing; waits otherwise
     QsJob& J = S.jobs[k][njobs[k]++];
     J.keys = q.d_keys;
@@ -433,6 +447,23 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
     e = run_width<uint64_t>(s, 0, nparts[0], njobs[0], nsegs[0], max_open[0], max_small[0]);
   if (e == cudaSuccess)
     e = run_width<uint32_t>(s, 1, nparts[1], njobs[1], nsegs[1], max_open[1], max_small[1]);
+  // sorts in their tail: every open item sorted completely (median-of-15 pivots,
+  // as in the levels)
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    for (uint64_t id : tail_ids[k]) {
+      Req& q = s->reqs[id];
+      e = k == 0 ? lp::launch_qs_local<uint64_t>(static_cast<uint64_t*>(q.d_keys),
+                                                 q.lists[q.cur], (uint32_t)q.open, q.level,
+                                                 q.r.seed, lp::kQsSamplesMax, s->d_tail,
+                                                 s->d_ctl + 2, s->tail_grid[0], st)
+                 : lp::launch_qs_local<uint32_t>(static_cast<uint32_t*>(q.d_keys),
+                                                 q.lists[q.cur], (uint32_t)q.open, q.level,
+                                                 q.r.seed, lp::kQsSamplesMax, s->d_tail + 8,
+                                                 s->d_ctl + 3, s->tail_grid[1], st);
+      if (e != cudaSuccess) break;
+      s->stats.launches += 2;
+    }
+  }
   // ---- read back: level counts of every slot, partition splits, status
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(S.lc_back, s->d_lc, slots * sizeof(QsLevelCounts),
@@ -478,7 +509,14 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
       q.level++;
       q.cur ^= 1;
       q.open = S.lc_back[q.slot].next;
+      q.max_next = S.lc_back[q.slot].max_next;
+      if (q.open > q.peak_open) q.peak_open = q.open;
       if (q.open == 0) finished.push_back(id);
+    }
+    for (uint64_t id : tail_ids[k]) {  // sorted completely this step
+      Req& q = s->reqs[id];
+      q.steps++;
+      finished.push_back(id);
     }
   }
   for (uint64_t id : finished) {
@@ -608,6 +646,10 @@ lp_status lp_server_create(int device, const lp_server_config* cfg, lp_server** 
   s->d_acc = reinterpret_cast<unsigned long long*>(take(256));
   s->d_begin = reinterpret_cast<QsBegin*>(take((size_t)slots * sizeof(QsBegin)));
   s->d_ctl = reinterpret_cast<uint32_t*>(take(256));
+  s->d_tail = reinterpret_cast<unsigned long long*>(take(256));
+  if (lp::qs_local_grid<uint64_t>(device, &s->tail_grid[0]) != cudaSuccess ||
+      lp::qs_local_grid<uint32_t>(device, &s->tail_grid[1]) != cudaSuccess)
+    return fail(LP_ERR_CUDA);
   // the batched launches of both widths share the barrier and status words
   // the batched launches of both widths share the barrier words; each has
   // its own status word (a launch resets its own)
