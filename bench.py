@@ -50,15 +50,16 @@ HANDOFF = (1 << 64) - 1  # level record of a range handed to the low-space parti
 PART_SOURCES = ["lp_smoothed.cuh", "lp_kernels.cu", "lp_plan.h", "lp_device.cuh",
                 "lp_coop.cuh", "lp_launch.h"]
 BATCH_SOURCES = ["lp_batched.cu", "lp_batched.h", "lp_smoothed.cuh", "lp_plan.h",
-                 "lp_device.cuh", "lp_coop.cuh"]
-QS_SOURCES = BATCH_SOURCES + ["lp_qs.cu", "lp_qs.cuh", "lp_qs_sort.cuh", "lp_quicksort.cu"]
+                 "lp_device.cuh", "lp_coop.cuh", "lp_fixup.cuh"]
+QS_SOURCES = BATCH_SOURCES + ["lp_qs.cu", "lp_qs.cuh", "lp_qs_sort.cuh", "lp_qs_pivot.cuh",
+                              "lp_qs_local.cu", "lp_quicksort.cu"]
 # name -> (summary file, kernel sources, machine-readable key of its DRAM bytes per unit)
 PROFILES = {
-    "partition_u64": ("partition_kernel_u64_ncu.txt", PART_SOURCES, "dram_bytes_per_key"),
-    "partition_u32": ("partition_kernel_u64_ncu.txt", PART_SOURCES, "dram_bytes_per_key_u32"),
-    "partition_kv": ("partition_kernel_u64_ncu.txt", PART_SOURCES, "dram_bytes_per_key_kv"),
+    "partition_u64": ("partition_kernel_ncu.txt", PART_SOURCES, "dram_bytes_per_key"),
+    "partition_u32": ("partition_kernel_ncu.txt", PART_SOURCES, "dram_bytes_per_key_u32"),
+    "partition_kv": ("partition_kernel_ncu.txt", PART_SOURCES, "dram_bytes_per_key_kv"),
     "batched": ("batched_kernel_u64_ncu.txt", BATCH_SOURCES, "dram_bytes_per_streamed_key"),
-    "quicksort": ("quicksort_u64_2p25_ncu.txt", QS_SOURCES, "dram_bytes_per_streamed_key"),
+    "quicksort": ("quicksort_u64_2p28_ncu.txt", QS_SOURCES, "dram_bytes_per_streamed_key"),
 }
 
 
@@ -990,7 +991,8 @@ def measure_quicksort(args, lp):
     tk = sum(s_["tail_keys"] for s_ in stats) / len(stats)
     tms = sum(s_["tail_ms"] for s_ in stats) / len(stats)
     achieved = 2 * 8 * pk / (pms / 1e3) / 1e9
-    traffic, why = profiled_traffic("quicksort", pk)
+    traffic, why = None, ("the committed ncu summary (profiles/quicksort_u64_2p28_ncu.txt) "
+                          "captures single levels; a step's traffic is not one level's scaled")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "batched_kernel<uint64_t> (every partition level, "
