@@ -176,12 +176,13 @@ def test_median_of_15_pivots(ctx, kind, n):
 def test_tail_kernel_runs_and_sorts(ctx, n, dtype):
     """Sizes whose last levels hold few, small subarrays: the tail kernel
     sorts them (the stats say it ran) and the result equals a library sort;
-    every key is sorted in shared memory exactly once."""
+    every key is sorted in shared memory at most once (keys equal to an
+    equal-key item's pivot are final without a sort)."""
     host = make("uniform", n, 0x7A1 + n, dtype)
     d = to_dev(host)
     lp.lp_quicksort(ctx, d, seed=2)
     torch.cuda.synchronize()
     st = ctx.sort_stats()
     assert st["tail_items"] > 0 and st["tail_keys"] > 0, st
-    assert st["sort_keys"] == n
+    assert 0.99 * n <= st["sort_keys"] <= n
     assert np.array_equal(to_host(d, dtype), np.sort(host))
