@@ -16,6 +16,24 @@
 #include "lp_plan.h"
 #include "lp_trace.h"
 
+const char* lp_timeout_what(uint32_t st) {
+  static thread_local char msg[160];
+  static const struct { uint32_t bit; const char* name; } sites[] = {
+      {lp::kSitePartition, "partition barrier"}, {lp::kSiteLowspace, "low-space barrier"},
+      {lp::kSiteRounds, "engine round barrier"},  {lp::kSiteSortLoop, "sort level barrier"},
+      {lp::kSiteLine, "line copy"},               {lp::kSiteBulk, "range copy"}};
+  int o = snprintf(msg, sizeof(msg), "device wait timed out");
+  const char* sep = " (";
+  for (const auto& x : sites) {
+    if ((st & x.bit) && o > 0 && o < (int)sizeof(msg)) {
+      o += snprintf(msg + o, sizeof(msg) - o, "%s%s", sep, x.name);
+      sep = ", ";
+    }
+  }
+  if (sep[0] == ',' && o > 0 && o < (int)sizeof(msg)) snprintf(msg + o, sizeof(msg) - o, ")");
+  return msg;
+}
+
 lp_status lp_fail(lp_ctx* c, lp_status s, const char* what) {
   if (c) c->err = what;
   return s;
@@ -37,7 +55,7 @@ inline lp_status cuda_fail(lp_ctx* c, cudaError_t e, const char* where) {
 
 lp_status status_to_lp(lp_ctx* c, uint32_t st) {
   if (st == 0) return LP_OK;
-  if (st & lp::kStatTimeout) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (st & lp::kStatTimeout) return fail(c, LP_ERR_TIMEOUT, lp_timeout_what(st));
   return fail(c, LP_ERR_INTERNAL, "device consistency check failed");
 }
 

@@ -227,7 +227,7 @@ lp_status lp_batch_wait(lp_batch* b, cudaStream_t stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "wait");
   const uint32_t st = (uint32_t)(c->h_pinned[7] & 0xffffffffu);
-  if (st & lp::kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (st & lp::kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, lp_timeout_what(st));
   if (st) return lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed");
   return LP_OK;
 }
@@ -353,7 +353,7 @@ lp_status quicksort_impl(lp_ctx* c, T* keys, uint64_t n, uint64_t seed, uint32_t
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return lp_cuda_fail(c, e, "read status");
   const uint32_t st = (uint32_t)(c->h_pinned[0] & 0xffffffffu);
-  if (st & lp::kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (st & lp::kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, lp_timeout_what(st));
   if (st) return lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed");
   return LP_OK;
 }

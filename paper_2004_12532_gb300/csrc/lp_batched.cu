@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
   // grid barrier; false (status set) if this CTA gave up waiting
   auto sync_grid = [&]() -> bool {
     if (grid_barrier(S.bar, gridDim.x, &flag)) return true;
-    if (tid == 0) atomicOr(S.status, kStatTimeout);
+    if (tid == 0) atomicOr(S.status, kStatTimeout | kSiteRounds);
     return false;
   };
   const bool stamp = blockIdx.x == 0 && tid == 0;

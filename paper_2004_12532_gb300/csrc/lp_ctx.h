@@ -48,6 +48,8 @@ void hostpart_free(lp_ctx* c);
 
 
 lp_status lp_fail(lp_ctx* c, lp_status s, const char* what);
+// "device wait timed out" and the kinds of wait that gave up (status word bits).
+const char* lp_timeout_what(uint32_t status);
 lp_status lp_cuda_fail(lp_ctx* c, cudaError_t e, const char* where);
 lp_status ensure_var(lp_ctx* c, size_t bytes, cudaStream_t stream);
 lp_status ensure_events(lp_ctx* c);

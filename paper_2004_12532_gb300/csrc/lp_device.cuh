@@ -15,6 +15,16 @@ enum : uint32_t {
   kStatUnfinished = 4u,  // a range was still open after the last level
   kStatBadArg = 8u,
 };
+// Where a bounded wait gave up: raised with kStatTimeout, one bit per kind of
+// wait, so that the host can say which one.
+enum : uint32_t {
+  kSitePartition = 1u << 16,  // a grid barrier of the single partition
+  kSiteLowspace = 1u << 17,   // a grid barrier of the low-space partition
+  kSiteRounds = 1u << 18,     // a grid barrier of the batched engine's rounds
+  kSiteSortLoop = 1u << 19,   // a grid barrier of the quicksort's level loop
+  kSiteLine = 1u << 20,       // a warp's wait for a line's bulk copy
+  kSiteBulk = 1u << 21,       // a CTA's wait for a range's bulk copy
+};
 
 // Wall-clock limit of any single wait, in ns (about one second).
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
@@ -130,10 +140,13 @@ __device__ __forceinline__ void bulk_wait_all() {
 // counts arrivals, bar[1] is the generation; both start at zero.  The last
 // CTA to arrive resets the count and advances the generation; the others wait
 // for the generation to change, for at most limit_ns.  Returns false (in
-// every thread of the CTA) if this CTA gave up waiting.
+// every thread of the CTA) if this CTA gave up waiting.  Proxy fences on both
+// sides order the plain stores before the barrier with the bulk copies
+// (async proxy) after it, in every CTA.
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks,
                                              unsigned int* flag_smem,
                                              uint64_t limit_ns = kWaitLimitNs) {
+  fence_proxy_async_global();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int ok = 1u;
@@ -155,6 +168,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nbl
     *flag_smem = ok;
   }
   __syncthreads();
+  fence_proxy_async_global();
   return *flag_smem != 0u;
 }
 

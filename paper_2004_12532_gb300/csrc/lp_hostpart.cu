@@ -194,7 +194,7 @@ lp_status host_partition(lp_ctx* c, T* host, uint64_t n, T pivot, uint64_t seed,
     // a chunk whose partition failed on the device, or whose split cannot be
     // one, plans no copy back: stop before the caller's array is written from it
     status |= (uint32_t)(H.h_slots[2 * j + 1] & 0xffffffffu);
-    if (status & kStatTimeout) return bail(lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out"));
+    if (status & kStatTimeout) return bail(lp_fail(c, LP_ERR_TIMEOUT, lp_timeout_what(status)));
     if (status) return bail(lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed"));
     if (!plan.partitioned(H.h_slots[2 * j]))
       return bail(lp_fail(c, LP_ERR_INTERNAL, "a chunk's split exceeds its length"));
@@ -213,7 +213,7 @@ lp_status host_partition(lp_ctx* c, T* host, uint64_t n, T pivot, uint64_t seed,
     return bail(lp_cuda_fail(c, e, "finish the copies back"));
   c->last_launches = cfg.launches;
   *split_out = plan.split();
-  if (status & kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (status & kStatTimeout) return lp_fail(c, LP_ERR_TIMEOUT, lp_timeout_what(status));
   if (status) return lp_fail(c, LP_ERR_INTERNAL, "device consistency check failed");
   return LP_OK;
 }

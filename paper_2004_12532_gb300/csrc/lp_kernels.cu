@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
       __syncthreads();
       const uint64_t t = coop_finish<T, KV>(base, vbase, n, pivot, S, smem_raw, &bar_flag);
       if (t == ~0ull) {
-        if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout);
+        if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout | kSitePartition);
       } else if (leader) {
         S.desc[L].vmin = lo + t;
         S.desc[L].vmax = lo + t;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(Tr<T, KV>::Threads, 2) partition_kernel(T* key
     if (!grid_barrier(S.bar, gridDim.x, &bar_flag,
                       g == 1 ? wait_limit_for_bytes(n * (R::K + (KV ? 8u : 0u)))
                              : kWaitLimitNs)) {
-      if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout);
+      if (threadIdx.x == 0) atomicOr(S.status, kStatTimeout | kSitePartition);
       break;
     }
     // stop on an error raised anywhere in this level; one thread reads the

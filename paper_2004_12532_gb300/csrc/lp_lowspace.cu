@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   const uint64_t gtid = (uint64_t)blockIdx.x * kLT + tid, gstride = (uint64_t)gridDim.x * kLT;
   const bool leader = blockIdx.x == 0 && tid == 0;
   auto fail = [&]() {
-    if (tid == 0) atomicOr(S.status, kStatTimeout);
+    if (tid == 0) atomicOr(S.status, kStatTimeout | kSiteLowspace);
   };
 
   uint64_t lo = a.lo, hi = a.hi;
@@ -554,6 +554,17 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   // targets do.
   constexpr uint32_t kRU = KV ? 4 : (sizeof(T) == 4 ? 2 * kUnroll : kUnroll);
   static_assert(IMP ? 32 * kRU >= 2 * (kMaxValueBits + 1) : true, "a block's value in one round");
+  // Keys only, explicit counters: a block's targets are one contiguous range
+  // starting at v[i-1], so a round's targets are the window [y, y + 32 kRU)
+  // -- known once the round before has been ranked.  That window is loaded
+  // with the round's keys, a round ahead, and staged in the warp's shared
+  // memory (free during this phase), so no round waits on its target loads.
+  // Targets are disjoint from the sources and from other blocks' targets, so
+  // reading them a round early is safe.
+  constexpr bool kWin = !IMP && !KV;
+  static_assert(!kWin || (kLT / 32) * 32 * kRU * sizeof(T) <= level_smem_bytes<T, KV>(),
+                "the target windows fit the dynamic shared memory");
+  T* const tw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * kRU);
   const uint32_t lt = (1u << lane) - 1u;
   const unsigned long long* V = reinterpret_cast<const unsigned long long*>(a.v);
   for (int j = L - 1; j >= 0; j--) {
@@ -563,10 +574,15 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
       uint64_t r0 = i * B, e = (i + 1 == NB) ? M : r0 + B;
       uint64_t y = IMP ? 0 : __ldcg(&V[i - 1]);  // kept in key order: read below
       T x[kRU];
+      T w[kWin ? kRU : 1];  // the round's target window, lane l holding y + 32 u + l
 #pragma unroll
       for (uint32_t u = 0; u < kRU; u++) {
         const uint64_t q = r0 + 32ull * u + lane;
         if (q < e) x[u] = ldcg(&A[mem(q)]);
+        if constexpr (kWin) {
+          const uint64_t qt = y + 32ull * u + lane;
+          if (qt < n) w[u] = ldcg(&A[mem(qt)]);
+        }
       }
       for (;;) {
         // the next round: the rest of this block, else the warp's next block
@@ -615,6 +631,12 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
             y = val;
           }
         }
+        if constexpr (kWin) {  // the round's target window into shared memory
+          __syncwarp();
+#pragma unroll
+          for (uint32_t u = 0; u < kRU; u++) tw[32 * u + lane] = w[u];
+          __syncwarp();
+        }
         uint32_t f = 0;
 #pragma unroll
         for (uint32_t u = 0; u < kRU; u++)
@@ -628,11 +650,15 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
           const uint32_t bal = __ballot_sync(0xffffffffu, (f >> u) & 1u);
           tg[u] = run + __popc(bal & lt);
           if ((f >> u) & 1u) {
-            const uint64_t pt = mem(y + tg[u]);
-            z[u] = ldcg(&A[pt]);
-            if constexpr (KV) {
-              pz[u] = ldcg(&Y[pt]);
-              py[u] = ldcg(&Y[mem(r0 + 32ull * u + lane)]);
+            if constexpr (kWin) {
+              z[u] = tw[tg[u]];
+            } else {
+              const uint64_t pt = mem(y + tg[u]);
+              z[u] = ldcg(&A[pt]);
+              if constexpr (KV) {
+                pz[u] = ldcg(&Y[pt]);
+                py[u] = ldcg(&Y[mem(r0 + 32ull * u + lane)]);
+              }
             }
           }
           run += __popc(bal);
@@ -640,12 +666,16 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         T xn[kRU];
         uint64_t yn = y + run;
         if (more) {
+          if (next_block) yn = IMP ? 0 : __ldcg(&V[i1 - 1]);
 #pragma unroll
           for (uint32_t u = 0; u < kRU; u++) {
             const uint64_t q = r1 + 32ull * u + lane;
             if (q < e1) xn[u] = ldcg(&A[mem(q)]);
+            if constexpr (kWin) {  // the next round's targets start at yn
+              const uint64_t qt = yn + 32ull * u + lane;
+              if (qt < n) w[u] = ldcg(&A[mem(qt)]);
+            }
           }
-          if (next_block) yn = IMP ? 0 : __ldcg(&V[i1 - 1]);
         }
 #pragma unroll
         for (uint32_t u = 0; u < kRU; u++) {

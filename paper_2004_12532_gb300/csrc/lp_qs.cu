@@ -6,7 +6,7 @@
 #include <stdint.h>
 
 #include "lp_qs.cuh"
-#include "lp_qs_pivot.cuh"
+#include "lp_qs_level.cuh"
 #include "lp_qs_sort.cuh"
 
 namespace lp {
@@ -19,32 +19,8 @@ __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
   const QsJob& J = jobs[blockIdx.y];
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= J.count) return;
-  const QsItem q = J.items[i];
-  T* keys = static_cast<T*>(J.keys);
-  const uint64_t h = qs_item_hash(J.seed, J.level, q.lo, q.n);
-  SegDesc d = {};
-  d.keys = keys + q.lo;
-  d.n = q.n;
-  if (q.eq) {
-    d.pivot = q.pivot - 1;  // q.pivot > 0: a zero pivot never makes an equal-key item
-  } else {
-    d.pivot = (uint64_t)(J.samples == kQsSamplesMax ? qs_median<kQsSamplesMax>(keys, q.lo, q.n, h)
-                                                    : qs_median<3>(keys, q.lo, q.n, h));
-  }
-  // the subarray and level name it, not its place in the list
-  d.salt = sm_stream(h, kQsSamplesMax + 1);
-  segs[J.seg_base + i] = d;
-}
-
-__device__ __forceinline__ void qs_push(const QsJob& J, uint64_t lo, uint64_t n) {
-  if (n <= 1) return;  // a single key is in place
-  if (n <= (J.local_cut ? (uint64_t)J.local_cut : kQsCut)) {
-    J.small[atomicAdd(&J.lc->small, 1u)] = QsSmall{lo, n, J.level + 1, 0u};
-    atomicAdd(J.sort_keys, (unsigned long long)n);
-  } else {
-    J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{lo, n, 0, 0};
-    atomicMax(&J.lc->max_next, n < 0xffffffffull ? (uint32_t)n : 0xffffffffu);
-  }
+  segs[J.seg_base + i] =
+      qs_item_record<T>(static_cast<T*>(J.keys), J.items[i], J.seed, J.level, J.samples);
 }
 
 __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const uint64_t* splits,
@@ -54,22 +30,7 @@ __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const ui
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *traffic_acc += *traffic;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= J.count) return;
-  const QsItem q = J.items[i];
-  const uint64_t t = splits[J.seg_base + i];
-  if (q.eq) {  // [lo, lo + t) < p; the rest equals p
-    qs_push(J, q.lo, t);
-    return;
-  }
-  if (t == q.n) {  // no successor: split off the keys equal to the pivot next level
-    const uint64_t p = segs[J.seg_base + i].pivot;
-    if (p != 0) {
-      J.next[atomicAdd(&J.lc->next, 1u)] = QsItem{q.lo, q.n, p, 1};
-      atomicMax(&J.lc->max_next, q.n < 0xffffffffull ? (uint32_t)q.n : 0xffffffffu);
-    }
-    return;
-  }
-  qs_push(J, q.lo, t);
-  qs_push(J, q.lo + t, q.n - t);
+  qs_item_children(J, J.items[i], splits[J.seg_base + i], segs[J.seg_base + i].pivot);
 }
 
 template <typename T>

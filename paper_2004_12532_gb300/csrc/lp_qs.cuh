@@ -33,9 +33,9 @@ struct QsItem {
   uint64_t eq;            // 1: equal-key item
 };
 struct QsSmall {
-  uint64_t lo, n;
+  uint64_t lo;
+  uint32_t n;      // at most kQsCut (or the job's local_cut)
   uint32_t level;  // the subarray's level (names its pivot when it is partitioned further)
-  uint32_t pad;
 };
 // per-job list sizes of the current level (reset every level), in device memory
 struct QsLevelCounts {

@@ -10,8 +10,8 @@
 // level's small subarrays, read the next list's size back (one host
 // synchronisation per level).  Auxiliary memory: two item lists of at most
 // n / (kQsCut + 1) items (32 bytes each), a small list of twice that (16
-// bytes each), and the records of one slice -- about 0.4% of a uint64 array's
-// bytes at n = 2^28, plus a fixed ~2.4 MB.
+// bytes each), and the records of one slice of at most kSlice items (about
+// 2.9 MB) -- about 0.4% of a uint64 array's bytes at n = 2^28.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -99,7 +99,7 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
     e = cudaMemcpyAsync(L.lists[0], &whole, sizeof(whole), cudaMemcpyHostToDevice, st);
     open = 1;
   } else {
-    const QsSmall whole{0, n, 0u, 0u};
+    const QsSmall whole{0, (uint32_t)n, 0u};
     e = cudaMemcpyAsync(L.small, &whole, sizeof(whole), cudaMemcpyHostToDevice, st);
   }
   if (e != cudaSuccess) return e;

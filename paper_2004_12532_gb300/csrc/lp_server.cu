@@ -65,7 +65,7 @@ __global__ void qs_begin_kernel(const QsBegin* b, uint32_t count) {
   QsLevelCounts c{0u, 0u};
   if (x.mode == 1) x.list0[0] = QsItem{0, x.n, 0, 0};
   if (x.mode == 2) {
-    x.small[0] = QsSmall{0, x.n, 0u, 0u};
+    x.small[0] = QsSmall{0, (uint32_t)x.n, 0u};
     c.small = 1u;
   }
   *x.lc = c;
@@ -479,8 +479,9 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
   const uint32_t dev_status = S.status_back[0] | S.status_back[1];
   if (dev_status != 0) {
     s->broken = true;
-    return srv_fail(s, (dev_status & lp::kStatTimeout) ? LP_ERR_TIMEOUT : LP_ERR_INTERNAL,
-                    "device status after an engine step");
+    const bool timeout = (dev_status & lp::kStatTimeout) != 0;
+    return srv_fail(s, timeout ? LP_ERR_TIMEOUT : LP_ERR_INTERNAL,
+                    timeout ? lp_timeout_what(dev_status) : "device status after an engine step");
   }
   s->stats.steps++;
   for (int k = 0; k < 2; k++) {

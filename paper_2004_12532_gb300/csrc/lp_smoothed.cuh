@@ -364,7 +364,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     // drain this warp's loads still in flight with bounded waits; the array
     // is left in an unspecified state and the status word says why
     if (lane == 0) {
-      atomicOr(status, kStatTimeout);
+      atomicOr(status, kStatTimeout | kSiteLine);
       for (int32_t l = c.fnext; l <= c.bnext; l++) {
         if (l >= c.fi && l <= c.bi) continue;  // never issued
         const uint32_t s2 = pair_stage_of<R::Q>(c, l);
@@ -519,7 +519,7 @@ __device__ uint32_t cta_bulk_stage(const T* __restrict__ keys, uint32_t n, T piv
   }
   const bool ok = mbar_wait_bounded(bar, parity);
   if (!ok) {
-    if (tid == 0) atomicOr(status, kStatTimeout);
+    if (tid == 0) atomicOr(status, kStatTimeout | kSiteBulk);
     mbar_wait_bounded(bar, parity);  // let the copy land before the memory is reused
     __syncthreads();
     return ~0u;
