@@ -554,14 +554,16 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   // targets do.
   constexpr uint32_t kRU = KV ? 4 : (sizeof(T) == 4 ? 2 * kUnroll : kUnroll);
   static_assert(IMP ? 32 * kRU >= 2 * (kMaxValueBits + 1) : true, "a block's value in one round");
-  // Keys only, explicit counters: a block's targets are one contiguous range
-  // starting at v[i-1], so a round's targets are the window [y, y + 32 kRU)
-  // -- known once the round before has been ranked.  That window is loaded
-  // with the round's keys, a round ahead, and staged in the warp's shared
-  // memory (free during this phase), so no round waits on its target loads.
-  // Targets are disjoint from the sources and from other blocks' targets, so
-  // reading them a round early is safe.
-  constexpr bool kWin = !IMP && !KV;
+  // 8-byte keys only, explicit counters: a block's targets are one
+  // contiguous range starting at v[i-1], so a round's targets are the window
+  // [y, y + 32 kRU) -- known once the round before has been ranked.  That
+  // window is loaded with the round's keys, a round ahead, and staged in the
+  // warp's shared memory (free during this phase), so no round waits on its
+  // target loads.  Targets are disjoint from the sources and from other
+  // blocks' targets, so reading them a round early is safe.  (4-byte keys
+  // take rounds of twice the keys; holding their window as well costs more
+  // registers than the wait it saves.)
+  constexpr bool kWin = !IMP && !KV && sizeof(T) == 8;
   static_assert(!kWin || (kLT / 32) * 32 * kRU * sizeof(T) <= level_smem_bytes<T, KV>(),
                 "the target windows fit the dynamic shared memory");
   T* const tw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * kRU);

@@ -117,7 +117,7 @@ struct LineReg {
   T x[Tr<T, KV>::VPL][Tr<T, KV>::V];
   uint64_t y[KV ? Tr<T, KV>::VPL : 1][KV ? Tr<T, KV>::V : 1];
   uint32_t pred;   // bit u*V+v: key (u, v) is a predecessor
-  uint32_t valid;  // bit u: vector u*32 + lane exists
+  uint32_t keys;   // bit u*V+v: key (u, v) exists (vector u*32 + lane is in the line)
   uint32_t gl;     // line index within the range (warp-uniform)
   uint32_t len;    // keys in the line (warp-uniform)
 };
@@ -137,6 +137,8 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
   using R = Tr<T, KV>;
   constexpr uint32_t V = R::V, VPL = R::VPL, NB = VPL * V;
   constexpr uint32_t FULL = 0xffffffffu;
+  static_assert(NB < 32, "slot masks of 32-bit words");
+  constexpr uint32_t kAllSlots = (1u << NB) - 1u;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
   k = 0;
@@ -196,23 +198,33 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     Lr.gl = sm.st_line[st];
     Lr.len = sm.st_len[st];
     const uint32_t nvec = Lr.len / V;
-    uint32_t pred = 0, valid = 0;
-#pragma unroll
-    for (uint32_t u = 0; u < VPL; u++) {
+    uint32_t pred = 0, keys = 0;
+    auto load_vector = [&](uint32_t u) {
       const uint32_t vec = u * 32u + lane;
-      if (vec < nvec) {
-        valid |= 1u << u;
-        load_vec<T>(&sm.stage[st][vec * V], Lr.x[u]);
-        if constexpr (KV) {
-          const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&sm.vstage[st][vec * V]);
-          Lr.y[u][0] = w.x; Lr.y[u][1] = w.y;
-        }
+      load_vec<T>(&sm.stage[st][vec * V], Lr.x[u]);
+      if constexpr (KV) {
+        const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&sm.vstage[st][vec * V]);
+        Lr.y[u][0] = w.x; Lr.y[u][1] = w.y;
+      }
 #pragma unroll
-        for (uint32_t v = 0; v < V; v++) pred |= (Lr.x[u][v] <= pivot ? 1u : 0u) << (u * V + v);
+      for (uint32_t v = 0; v < V; v++) pred |= (Lr.x[u][v] <= pivot ? 1u : 0u) << (u * V + v);
+    };
+    if (NB > 8 && Lr.len == R::LineKeys) {  // a full line (warp-uniform; 4-byte keys,
+                                            // ALU-bound): every vector exists
+#pragma unroll
+      for (uint32_t u = 0; u < VPL; u++) load_vector(u);
+      keys = kAllSlots;
+    } else {
+#pragma unroll
+      for (uint32_t u = 0; u < VPL; u++) {
+        if (u * 32u + lane < nvec) {
+          load_vector(u);
+          keys |= ((1u << V) - 1u) << (u * V);
+        }
       }
     }
     Lr.pred = pred;
-    Lr.valid = valid;
+    Lr.keys = keys;
     kl += __popc(pred);
     __syncwarp();  // every lane has read the stage: it may be refilled
     if (pair_can_issue(c)) {
@@ -223,16 +235,21 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
   };
   auto store_line = [&](const LineReg<T, KV>& Lr) {
     T* dst = base + (size_t)Lr.gl * b32;
-#pragma unroll
-    for (uint32_t u = 0; u < VPL; u++) {
-      if ((Lr.valid >> u) & 1u) {
-        const uint32_t vec = u * 32u + lane;
-        store_vec<T>(dst + vec * V, Lr.x[u]);
-        if constexpr (KV) {
-          *reinterpret_cast<ulonglong2*>(vbase + (size_t)Lr.gl * b32 + vec * V) =
-              make_ulonglong2(Lr.y[u][0], Lr.y[u][1]);
-        }
+    auto store_vector = [&](uint32_t u) {
+      const uint32_t vec = u * 32u + lane;
+      store_vec<T>(dst + vec * V, Lr.x[u]);
+      if constexpr (KV) {
+        *reinterpret_cast<ulonglong2*>(vbase + (size_t)Lr.gl * b32 + vec * V) =
+            make_ulonglong2(Lr.y[u][0], Lr.y[u][1]);
       }
+    };
+    if (NB > 8 && Lr.len == R::LineKeys) {  // a full line (warp-uniform; 4-byte keys)
+#pragma unroll
+      for (uint32_t u = 0; u < VPL; u++) store_vector(u);
+    } else {
+#pragma unroll
+      for (uint32_t u = 0; u < VPL; u++)
+        if ((Lr.keys >> (u * V)) & 1u) store_vector(u);
     }
   };
 
@@ -260,11 +277,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     // swap the j-th successor of L with the j-th predecessor of R, both
     // numbered lane by lane (slots in order within a lane): one warp scan of
     // the per-lane counts, packed (successors of L low, predecessors of R high)
-    uint32_t lkeys = 0;  // bit j: key slot j of L exists
-#pragma unroll
-    for (uint32_t u = 0; u < VPL; u++)
-      if ((Lr.valid >> u) & 1u) lkeys |= ((1u << V) - 1u) << (u * V);
-    const uint32_t lsucc = ~Lr.pred & lkeys;
+    const uint32_t lsucc = ~Lr.pred & Lr.keys;
     const uint32_t rpred = Rr.pred;
     const uint32_t own = (uint32_t)__popc(lsucc) | ((uint32_t)__popc(rpred) << 16);
     uint32_t incl = own;
@@ -279,44 +292,48 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     if (m > 0) {
       const uint32_t exl = (incl - own) & 0xffffu, exr = (incl - own) >> 16;
       if constexpr (NB > 8) {
-        // 16 slots per lane (4-byte keys, issue-bound): ranks by running
-        // counts; the slots that move form a prefix of each lane's
-        // successors of L (predecessors of R) in slot order
-        uint32_t cl = exl, cr = exr, ml = 0, mr = 0;
+        // 16 slots per lane (4-byte keys, ALU-bound).  Every wrong key of
+        // both lines goes to the exchange buffer at its rank (successors of
+        // L from exl on, predecessors of R from exr on, in slot order); only
+        // ranks below m are read back.  m = min(SL, PR), so one side's wrong
+        // keys all move and only the other's are a prefix -- a lane's movers
+        // there are the lowest of its wrong keys, cut in the one lane where
+        // rank m falls.  Pointers walk the buffer: one add per slot.
+        static_assert(!KV, "key + payload lines hold 8 slots per lane");
+        T* pl = &sm.xbuf[0][exl];
+        T* pr = &sm.xbuf[1][exr];
 #pragma unroll
         for (uint32_t j = 0; j < NB; j++) {
           const uint32_t u = j / V, v = j % V;
           const uint32_t bl = (lsucc >> j) & 1u, br = (rpred >> j) & 1u;
-          if (bl && cl < m) {
-            sm.xbuf[0][cl] = Lr.x[u][v];
-            if constexpr (KV) sm.vxbuf[0][cl] = Lr.y[u][v];
-            ml |= 1u << j;
-          }
-          if (br && cr < m) {
-            sm.xbuf[1][cr] = Rr.x[u][v];
-            if constexpr (KV) sm.vxbuf[1][cr] = Rr.y[u][v];
-            mr |= 1u << j;
-          }
-          cl += bl;
-          cr += br;
+          if (bl) *pl = Lr.x[u][v];
+          if (br) *pr = Rr.x[u][v];
+          pl += bl;
+          pr += br;
         }
+        // the movers: all wrong keys of the shorter side, the first m of the other
+        auto first_m = [&](uint32_t wrong, uint32_t ex) -> uint32_t {
+          const uint32_t have = (uint32_t)__popc(wrong);
+          if (ex >= m) return 0u;
+          if (ex + have <= m) return wrong;
+          uint32_t t = wrong;  // the lane holding rank m: keep its lowest m - ex
+          for (uint32_t c = m - ex; c > 0; c--) t &= t - 1u;
+          return wrong ^ t;
+        };
+        const uint32_t ml = SL <= PR ? lsucc : first_m(lsucc, exl);
+        const uint32_t mr = PR <= SL ? rpred : first_m(rpred, exr);
         __syncwarp();
-        cl = exl;
-        cr = exr;
+        // each side reads the other's keys at its own ranks
+        const T* ql = &sm.xbuf[1][exl];
+        const T* qr = &sm.xbuf[0][exr];
 #pragma unroll
         for (uint32_t j = 0; j < NB; j++) {
           const uint32_t u = j / V, v = j % V;
           const uint32_t bl = (ml >> j) & 1u, br = (mr >> j) & 1u;
-          if (bl) {
-            Lr.x[u][v] = sm.xbuf[1][cl];
-            if constexpr (KV) Lr.y[u][v] = sm.vxbuf[1][cl];
-          }
-          if (br) {
-            Rr.x[u][v] = sm.xbuf[0][cr];
-            if constexpr (KV) Rr.y[u][v] = sm.vxbuf[0][cr];
-          }
-          cl += bl;
-          cr += br;
+          if (bl) Lr.x[u][v] = *ql;
+          if (br) Rr.x[u][v] = *qr;
+          ql += bl;
+          qr += br;
         }
         Lr.pred |= ml;
         Rr.pred &= ~mr;
@@ -391,7 +408,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
 #pragma unroll
     for (uint32_t j = 0; j < NB; j++) {
       const uint32_t u = j / V, v = j % V;
-      const uint32_t bs = __ballot_sync(FULL, ((F.valid >> u) & 1u) && !((F.pred >> j) & 1u));
+      const uint32_t bs = __ballot_sync(FULL, ((F.keys >> j) & 1u) && !((F.pred >> j) & 1u));
       if ((bp[j] >> lane) & 1u) {
         const uint32_t pos = ap + __popc(bp[j] & lt);
         dst[pos] = F.x[u][v];
