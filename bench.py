@@ -52,7 +52,7 @@ PART_SOURCES = ["lp_smoothed.cuh", "lp_kernels.cu", "lp_plan.h", "lp_device.cuh"
 BATCH_SOURCES = ["lp_batched.cu", "lp_batched.h", "lp_smoothed.cuh", "lp_plan.h",
                  "lp_device.cuh", "lp_coop.cuh", "lp_fixup.cuh"]
 QS_SOURCES = BATCH_SOURCES + ["lp_qs.cu", "lp_qs.cuh", "lp_qs_sort.cuh", "lp_qs_pivot.cuh",
-                              "lp_qs_local.cu", "lp_quicksort.cu"]
+                              "lp_qs_level.cuh", "lp_qs_local.cu", "lp_quicksort.cu"]
 # name -> (summary file, kernel sources, machine-readable key of its DRAM bytes per unit)
 PROFILES = {
     "partition_u64": ("partition_kernel_ncu.txt", PART_SOURCES, "dram_bytes_per_key"),
