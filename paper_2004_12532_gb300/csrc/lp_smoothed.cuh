@@ -207,7 +207,8 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
         Lr.y[u][0] = w.x; Lr.y[u][1] = w.y;
       }
 #pragma unroll
-      for (uint32_t v = 0; v < V; v++) pred |= (Lr.x[u][v] <= pivot ? 1u : 0u) << (u * V + v);
+      for (uint32_t v = 0; v < V; v++)
+        if (Lr.x[u][v] <= pivot) pred |= 1u << (u * V + v);
     };
     if (NB > 8 && Lr.len == R::LineKeys) {  // a full line (warp-uniform; 4-byte keys,
                                             // ALU-bound): every vector exists
@@ -305,11 +306,8 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
 #pragma unroll
         for (uint32_t j = 0; j < NB; j++) {
           const uint32_t u = j / V, v = j % V;
-          const uint32_t bl = (lsucc >> j) & 1u, br = (rpred >> j) & 1u;
-          if (bl) *pl = Lr.x[u][v];
-          if (br) *pr = Rr.x[u][v];
-          pl += bl;
-          pr += br;
+          if ((lsucc >> j) & 1u) *pl++ = Lr.x[u][v];
+          if ((rpred >> j) & 1u) *pr++ = Rr.x[u][v];
         }
         // the movers: all wrong keys of the shorter side, the first m of the other
         auto first_m = [&](uint32_t wrong, uint32_t ex) -> uint32_t {
@@ -329,11 +327,8 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
 #pragma unroll
         for (uint32_t j = 0; j < NB; j++) {
           const uint32_t u = j / V, v = j % V;
-          const uint32_t bl = (ml >> j) & 1u, br = (mr >> j) & 1u;
-          if (bl) Lr.x[u][v] = *ql;
-          if (br) Rr.x[u][v] = *qr;
-          ql += bl;
-          qr += br;
+          if ((ml >> j) & 1u) Lr.x[u][v] = *ql++;
+          if ((mr >> j) & 1u) Rr.x[u][v] = *qr++;
         }
         Lr.pred |= ml;
         Rr.pred &= ~mr;
