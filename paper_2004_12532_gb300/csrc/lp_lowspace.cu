@@ -575,6 +575,9 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
     if (i < NB) {
       uint64_t r0 = i * B, e = (i + 1 == NB) ? M : r0 + B;
       uint64_t y = IMP ? 0 : __ldcg(&V[i - 1]);  // kept in key order: read below
+      // the end of the block's targets (window loads stop there: at a 1% or
+      // 99% pivot a round has a few targets, not 32 kRU)
+      uint64_t te = kWin ? __ldcg(&V[i]) : 0;
       T x[kRU];
       T w[kWin ? kRU : 1];  // the round's target window, lane l holding y + 32 u + l
 #pragma unroll
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         if (q < e) x[u] = ldcg(&A[mem(q)]);
         if constexpr (kWin) {
           const uint64_t qt = y + 32ull * u + lane;
-          if (qt < n) w[u] = ldcg(&A[mem(qt)]);
+          if (qt < te) w[u] = ldcg(&A[mem(qt)]);
         }
       }
       for (;;) {
@@ -668,14 +671,17 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         T xn[kRU];
         uint64_t yn = y + run;
         if (more) {
-          if (next_block) yn = IMP ? 0 : __ldcg(&V[i1 - 1]);
+          if (next_block) {
+            yn = IMP ? 0 : __ldcg(&V[i1 - 1]);
+            if constexpr (kWin) te = __ldcg(&V[i1]);
+          }
 #pragma unroll
           for (uint32_t u = 0; u < kRU; u++) {
             const uint64_t q = r1 + 32ull * u + lane;
             if (q < e1) xn[u] = ldcg(&A[mem(q)]);
             if constexpr (kWin) {  // the next round's targets start at yn
               const uint64_t qt = yn + 32ull * u + lane;
-              if (qt < n) w[u] = ldcg(&A[mem(qt)]);
+              if (qt < te) w[u] = ldcg(&A[mem(qt)]);
             }
           }
         }
