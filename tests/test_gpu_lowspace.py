@@ -119,3 +119,43 @@ def test_variants_kv_repeated(ctx, variant, frac):
         assert int((ko[:t] > p_signed).sum()) == 0 and int((ko[t:] <= p_signed).sum()) == 0
         assert torch.equal(torch.sort(kin)[0], torch.sort(keys)[0])  # a permutation
         assert torch.equal(kin[vals], keys)  # every payload still names its key
+
+
+def structured_u64(kind, n, seed):
+    """Inputs whose blocks hold no predecessors, only predecessors, or runs of
+    either: the Reorder's per-block target ranges are then empty, full, or
+    cut at block edges."""
+    rng = np.random.default_rng(seed)
+    u = inputs.uniform_u64(n, seed)
+    if kind == "sorted":
+        return np.sort(u)
+    if kind == "reverse":
+        return np.sort(u)[::-1].copy()
+    if kind == "equal":
+        return np.full(n, np.uint64(1 << 62), dtype=np.uint64)
+    if kind == "block_runs":  # runs of 4096 keys alternately below and above 2^63
+        lo = u >> np.uint64(1)
+        hi = lo | np.uint64(1 << 63)
+        run = (np.arange(n) // 4096) % 2 == 0
+        return np.where(run, lo, hi)
+    if kind == "ragged_runs":  # runs of random lengths alternately below and above 2^63
+        lens = rng.integers(1, 9000, size=n // 1000 + 2)
+        side = np.repeat(np.arange(lens.size) % 2 == 0, lens)[:n]
+        lo = u >> np.uint64(1)
+        return np.where(side, lo, lo | np.uint64(1 << 63))
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["sorted", "reverse", "equal", "block_runs", "ragged_runs"])
+@pytest.mark.parametrize("q", [(1, 100), (1, 2), (99, 100)])
+def test_lowspace_structured(ctx, kind, q):
+    """Default parameters (B = 4096, the innermost prefix on chip) on
+    (1 << 23) + 11 keys: several Reorder levels, blocks with no targets and
+    blocks whose targets fill several rounds; split and both sides' multisets
+    against the oracle."""
+    n = (1 << 23) + 11
+    host = structured_u64(kind, n, 41 + q[0])
+    pv = inputs.quantile_pivot(*q) if kind != "equal" else (1 << 62) - (q[0] == 1)
+    dev = to_dev(host)
+    t = lp.lp_partition_u64(ctx, dev, pv, lp.LP_LOWSPACE)
+    check_partition(to_host(dev, np.uint64), host, t, oracle.count(host, pv), pv)
