@@ -187,6 +187,36 @@ def test_partition_u32(ctx, n, offset):
     check_partition(out, host, t, oracle.count(host, pv), pv)
 
 
+@pytest.mark.parametrize("kind", ["uniform_q1", "uniform_q99", "sorted", "reverse", "equal",
+                                  "dup16", "period", "lines"])
+def test_partition_u32_patterns(ctx, kind):
+    """The 16-slot line swap of 4-byte keys on inputs that make one side's
+    wrong keys all move or only a prefix of them (every lane, or one), with
+    lines that are pure from the start and lines that are all wrong."""
+    n = (1 << 22) + 77
+    pv = inputs.quantile_pivot(1, 2, 32)
+    u = inputs.uniform_u32(n, 11)
+    if kind == "uniform_q1":
+        host, pv = u, inputs.quantile_pivot(1, 100, 32)
+    elif kind == "uniform_q99":
+        host, pv = u, inputs.quantile_pivot(99, 100, 32)
+    elif kind == "sorted":
+        host = np.sort(u)
+    elif kind == "reverse":
+        host = np.sort(u)[::-1].copy()
+    elif kind == "equal":
+        host = np.full(n, np.uint32(pv), dtype=np.uint32)
+    elif kind == "dup16":
+        host = (u & np.uint32(15)) << np.uint32(28)
+    elif kind == "period":
+        host = np.where((np.arange(n) // 1024) % 304 < 152, np.uint32(1), np.uint32(2**32 - 1))
+    else:
+        host = np.where((np.arange(n) // 512) % 2 == 0, np.uint32(0), np.uint32(2**32 - 1))
+    dev = to_dev(host)
+    t = lp.lp_partition_u32(ctx, dev, pv)
+    check_partition(to_host(dev, np.uint32), host, t, oracle.count(host, pv), pv)
+
+
 @pytest.mark.parametrize("n", [100, 4096, 4097, 300007, (1 << 21) + 11])
 @pytest.mark.parametrize("offset", [0, 1])
 def test_partition_kv(ctx, n, offset):
