@@ -293,13 +293,15 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
     if (m > 0) {
       const uint32_t exl = (incl - own) & 0xffffu, exr = (incl - own) >> 16;
       if constexpr (NB > 8) {
-        // 16 slots per lane (4-byte keys, ALU-bound).  Every wrong key of
-        // both lines goes to the exchange buffer at its rank (successors of
-        // L from exl on, predecessors of R from exr on, in slot order); only
-        // ranks below m are read back.  m = min(SL, PR), so one side's wrong
-        // keys all move and only the other's are a prefix -- a lane's movers
-        // there are the lowest of its wrong keys, cut in the one lane where
-        // rank m falls.  Pointers walk the buffer: one add per slot.
+        // 16 slots per lane (4-byte keys: the slot work, not HBM, bounds
+        // them).  Every wrong key of both lines goes to the exchange buffer
+        // at its rank (successors of L from exl on, predecessors of R from exr
+        // on, in slot order); only ranks below m are read back.  m =
+        // min(SL, PR), so the wrong keys of the side with fewer all move and
+        // the other side's movers are its lowest m ranks -- in each lane the
+        // lowest of its wrong keys, cut in the one lane where rank m falls.
+        // A pointer walks the buffer per side, stepping under the slot's own
+        // predicate together with its store or load.
         static_assert(!KV, "key + payload lines hold 8 slots per lane");
         T* pl = &sm.xbuf[0][exl];
         T* pr = &sm.xbuf[1][exr];
@@ -309,7 +311,7 @@ __device__ bool warp_pair_group(T* __restrict__ base, uint64_t* __restrict__ vba
           if ((lsucc >> j) & 1u) *pl++ = Lr.x[u][v];
           if ((rpred >> j) & 1u) *pr++ = Rr.x[u][v];
         }
-        // the movers: all wrong keys of the shorter side, the first m of the other
+        // the movers: all wrong keys of the side with fewer, the first m of the other
         auto first_m = [&](uint32_t wrong, uint32_t ex) -> uint32_t {
           const uint32_t have = (uint32_t)__popc(wrong);
           if (ex >= m) return 0u;
