@@ -557,16 +557,19 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   // 8-byte keys only, explicit counters: a block's targets are one
   // contiguous range starting at v[i-1], so a round's targets are the window
   // [y, y + 32 kRU) -- known once the round before has been ranked.  That
-  // window is loaded with the round's keys, a round ahead, and staged in the
-  // warp's shared memory (free during this phase), so no round waits on its
-  // target loads.  Targets are disjoint from the sources and from other
-  // blocks' targets, so reading them a round early is safe.  (4-byte keys
-  // take rounds of twice the keys; holding their window as well costs more
-  // registers than the wait it saves.)
-  constexpr bool kWin = !IMP && !KV && sizeof(T) == 8;
-  static_assert(!kWin || (kLT / 32) * 32 * kRU * sizeof(T) <= level_smem_bytes<T, KV>(),
+  // window (keys, and with payloads their values) is loaded with the round's
+  // keys (and with payloads the round's own values), a round ahead, and
+  // staged in the warp's shared memory (free during this phase), so no round
+  // waits on its target loads.  Targets are disjoint from the sources and from
+  // other blocks' targets, so reading them a round early is safe.  (4-byte
+  // keys take rounds of twice the keys; holding their window as well costs
+  // more registers than the wait it saves.)
+  constexpr bool kWin = !IMP && sizeof(T) == 8;
+  static_assert(!kWin || (kLT / 32) * 32 * kRU * (sizeof(T) + (KV ? 8 : 0)) <=
+                             level_smem_bytes<T, KV>(),
                 "the target windows fit the dynamic shared memory");
-  T* const tw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * kRU);
+  T* const tw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * kRU) * (KV ? 2 : 1);
+  uint64_t* const twv = reinterpret_cast<uint64_t*>(tw + 32 * kRU);  // values (payloads only)
   const uint32_t lt = (1u << lane) - 1u;
   const unsigned long long* V = reinterpret_cast<const unsigned long long*>(a.v);
   for (int j = L - 1; j >= 0; j--) {
@@ -580,13 +583,21 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
       uint64_t te = kWin ? __ldcg(&V[i]) : 0;
       T x[kRU];
       T w[kWin ? kRU : 1];  // the round's target window, lane l holding y + 32 u + l
+      constexpr bool kWV = kWin && KV;
+      uint64_t xv[kWV ? kRU : 1], wv[kWV ? kRU : 1];  // the round's values, the window's
 #pragma unroll
       for (uint32_t u = 0; u < kRU; u++) {
         const uint64_t q = r0 + 32ull * u + lane;
-        if (q < e) x[u] = ldcg(&A[mem(q)]);
+        if (q < e) {
+          x[u] = ldcg(&A[mem(q)]);
+          if constexpr (kWV) xv[u] = ldcg(&Y[mem(q)]);
+        }
         if constexpr (kWin) {
           const uint64_t qt = y + 32ull * u + lane;
-          if (qt < te) w[u] = ldcg(&A[mem(qt)]);
+          if (qt < te) {
+            w[u] = ldcg(&A[mem(qt)]);
+            if constexpr (kWV) wv[u] = ldcg(&Y[mem(qt)]);
+          }
         }
       }
       for (;;) {
@@ -639,7 +650,10 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         if constexpr (kWin) {  // the round's target window into shared memory
           __syncwarp();
 #pragma unroll
-          for (uint32_t u = 0; u < kRU; u++) tw[32 * u + lane] = w[u];
+          for (uint32_t u = 0; u < kRU; u++) {
+            tw[32 * u + lane] = w[u];
+            if constexpr (kWV) twv[32 * u + lane] = wv[u];
+          }
           __syncwarp();
         }
         uint32_t f = 0;
@@ -657,6 +671,10 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
           if ((f >> u) & 1u) {
             if constexpr (kWin) {
               z[u] = tw[tg[u]];
+              if constexpr (kWV) {
+                pz[u] = twv[tg[u]];
+                py[u] = xv[u];
+              }
             } else {
               const uint64_t pt = mem(y + tg[u]);
               z[u] = ldcg(&A[pt]);
@@ -669,6 +687,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
           run += __popc(bal);
         }
         T xn[kRU];
+        uint64_t xvn[kWV ? kRU : 1];
         uint64_t yn = y + run;
         if (more) {
           if (next_block) {
@@ -678,10 +697,16 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
 #pragma unroll
           for (uint32_t u = 0; u < kRU; u++) {
             const uint64_t q = r1 + 32ull * u + lane;
-            if (q < e1) xn[u] = ldcg(&A[mem(q)]);
+            if (q < e1) {
+              xn[u] = ldcg(&A[mem(q)]);
+              if constexpr (kWV) xvn[u] = ldcg(&Y[mem(q)]);
+            }
             if constexpr (kWin) {  // the next round's targets start at yn
               const uint64_t qt = yn + 32ull * u + lane;
-              if (qt < te) w[u] = ldcg(&A[mem(qt)]);
+              if (qt < te) {
+                w[u] = ldcg(&A[mem(qt)]);
+                if constexpr (kWV) wv[u] = ldcg(&Y[mem(qt)]);
+              }
             }
           }
         }
@@ -699,7 +724,10 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         }
         if (!more) break;
 #pragma unroll
-        for (uint32_t u = 0; u < kRU; u++) x[u] = xn[u];
+        for (uint32_t u = 0; u < kRU; u++) {
+          x[u] = xn[u];
+          if constexpr (kWV) xv[u] = xvn[u];
+        }
         i = i1;
         r0 = r1;
         e = e1;
