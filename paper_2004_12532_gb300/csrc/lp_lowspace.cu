@@ -554,22 +554,27 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
   // targets do.
   constexpr uint32_t kRU = KV ? 4 : (sizeof(T) == 4 ? 2 * kUnroll : kUnroll);
   static_assert(IMP ? 32 * kRU >= 2 * (kMaxValueBits + 1) : true, "a block's value in one round");
-  // 8-byte keys only, explicit counters: a block's targets are one
-  // contiguous range starting at v[i-1], so a round's targets are the window
-  // [y, y + 32 kRU) -- known once the round before has been ranked.  That
+  // Explicit counters: a block's targets are one contiguous range starting
+  // at v[i-1] and ending at v[i], so a round's targets lie in the window
+  // [y, y + 32 kWR) -- known once the round before has been ranked.  That
   // window (keys, and with payloads their values) is loaded with the round's
-  // keys (and with payloads the round's own values), a round ahead, and
-  // staged in the warp's shared memory (free during this phase), so no round
-  // waits on its target loads.  Targets are disjoint from the sources and from
-  // other blocks' targets, so reading them a round early is safe.  (4-byte
-  // keys take rounds of twice the keys; holding their window as well costs
-  // more registers than the wait it saves.)
-  constexpr bool kWin = !IMP && sizeof(T) == 8;
-  static_assert(!kWin || (kLT / 32) * 32 * kRU * (sizeof(T) + (KV ? 8 : 0)) <=
+  // keys (and with payloads the round's own values), a round ahead, up to the
+  // block's last target, and staged in the warp's shared memory (free during
+  // this phase), so no round waits on its target loads.  Targets are disjoint
+  // from the sources and from other blocks' targets, so reading them a round
+  // early is safe.  4-byte keys take rounds of twice the keys and a window of
+  // 10 rows (320 keys): the view's predecessors are at most half the keys, so
+  // a round's targets nearly always fit; a target past the window is loaded
+  // directly.
+  constexpr bool kWin = !IMP;
+  constexpr uint32_t kWR = sizeof(T) == 4 ? 10 : kRU;  // window rows
+  static_assert(kWR <= kRU, "a window of at most a round");
+  static_assert(!kWin || (kLT / 32) * 32 * kWR * (sizeof(T) + (KV ? 8 : 0)) <=
                              level_smem_bytes<T, KV>(),
                 "the target windows fit the dynamic shared memory");
-  T* const tw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * kRU) * (KV ? 2 : 1);
-  uint64_t* const twv = reinterpret_cast<uint64_t*>(tw + 32 * kRU);  // values (payloads only)
+  T* const tw = reinterpret_cast<T*>(smem_raw) +
+                (size_t)warp * (32 * kWR) * (KV ? 2 * sizeof(uint64_t) / sizeof(T) : 1);
+  uint64_t* const twv = reinterpret_cast<uint64_t*>(tw + 32 * kWR);  // values (payloads only)
   const uint32_t lt = (1u << lane) - 1u;
   const unsigned long long* V = reinterpret_cast<const unsigned long long*>(a.v);
   for (int j = L - 1; j >= 0; j--) {
@@ -582,9 +587,9 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
       // 99% pivot a round has a few targets, not 32 kRU)
       uint64_t te = kWin ? __ldcg(&V[i]) : 0;
       T x[kRU];
-      T w[kWin ? kRU : 1];  // the round's target window, lane l holding y + 32 u + l
+      T w[kWin ? kWR : 1];  // the round's target window, lane l holding y + 32 u + l
       constexpr bool kWV = kWin && KV;
-      uint64_t xv[kWV ? kRU : 1], wv[kWV ? kRU : 1];  // the round's values, the window's
+      uint64_t xv[kWV ? kRU : 1], wv[kWV ? kWR : 1];  // the round's values, the window's
 #pragma unroll
       for (uint32_t u = 0; u < kRU; u++) {
         const uint64_t q = r0 + 32ull * u + lane;
@@ -594,7 +599,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         }
         if constexpr (kWin) {
           const uint64_t qt = y + 32ull * u + lane;
-          if (qt < te) {
+          if (u < kWR && qt < te) {
             w[u] = ldcg(&A[mem(qt)]);
             if constexpr (kWV) wv[u] = ldcg(&Y[mem(qt)]);
           }
@@ -650,7 +655,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
         if constexpr (kWin) {  // the round's target window into shared memory
           __syncwarp();
 #pragma unroll
-          for (uint32_t u = 0; u < kRU; u++) {
+          for (uint32_t u = 0; u < kWR; u++) {
             tw[32 * u + lane] = w[u];
             if constexpr (kWV) twv[32 * u + lane] = wv[u];
           }
@@ -670,7 +675,11 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
           tg[u] = run + __popc(bal & lt);
           if ((f >> u) & 1u) {
             if constexpr (kWin) {
-              z[u] = tw[tg[u]];
+              if (kWR == kRU || tg[u] < 32 * kWR) {
+                z[u] = tw[tg[u]];
+              } else {  // past the window (4-byte keys, rare): load it here
+                z[u] = ldcg(&A[mem(y + tg[u])]);
+              }
               if constexpr (kWV) {
                 pz[u] = twv[tg[u]];
                 py[u] = xv[u];
@@ -703,7 +712,7 @@ __global__ void __launch_bounds__(kLT, 2) lowspace_kernel(T* keys, uint64_t* val
             }
             if constexpr (kWin) {  // the next round's targets start at yn
               const uint64_t qt = yn + 32ull * u + lane;
-              if (qt < te) {
+              if (u < kWR && qt < te) {
                 w[u] = ldcg(&A[mem(qt)]);
                 if constexpr (kWV) wv[u] = ldcg(&Y[mem(qt)]);
               }
