@@ -159,11 +159,12 @@ lp_status lp_partition_kv_u64_async(lp_ctx *ctx, uint64_t *keys, uint64_t *vals,
  * Many independent partitions in one persistent cooperative launch: segment
  * s is keys[0..n) of segs[s], partitioned by [x <= pivot] with the Recursive
  * Smoothed Striding scheme (a step per round on its open range, the range
- * finished on chip once one CTA can hold it).  Per segment the result is a
- * partition with split t_s written to d_splits[s] (device, count entries),
- * deterministic for a given batch, seed and tuning.  Segments must not
- * overlap.  Scratch: about 48 bytes per segment plus 12 bytes per segment of
- * plan space, held by ctx. */
+ * finished on chip once one CTA, or the shared memory of at most the launch's
+ * CTAs, can hold it).  Per segment the result is a partition with split t_s
+ * written to d_splits[s] (device, count entries), deterministic for a given
+ * batch, seed and tuning.  Segments must not overlap.  Scratch: about 144
+ * bytes per segment record plus 28 bytes per segment of plan space and 64 KB
+ * of slice counts, held by ctx. */
 typedef struct {
   uint64_t *keys; /* device pointer, naturally aligned */
   uint64_t n;
@@ -178,6 +179,9 @@ typedef struct {
   uint32_t min_chunks;    /* lines per group, at least */
   uint32_t group_workers; /* groups per segment step, at most */
   uint32_t min_chunks_residual; /* lines per group, at least, in steps after the first */
+  uint32_t onchip_slices; /* a range finished on chip by several CTAs spans at most this
+                             many CTAs' shared memory (0 = the launch's grid); below the
+                             grid it also shortens the windows their counts share */
 } lp_batch_tuning;
 
 /* One-shot: copies the segment list (host) to the device and runs the batch on

@@ -40,7 +40,8 @@ class lp_segment_u64(C.Structure):
 
 class lp_batch_tuning(C.Structure):
     _fields_ = [("ctas", C.c_uint32), ("line_bytes", C.c_uint32), ("min_chunks", C.c_uint32),
-                ("group_workers", C.c_uint32), ("min_chunks_residual", C.c_uint32)]
+                ("group_workers", C.c_uint32), ("min_chunks_residual", C.c_uint32),
+                ("onchip_slices", C.c_uint32)]
 
 
 class lp_sort_stats(C.Structure):
@@ -420,12 +421,14 @@ def lp_autotune_batched_u64(ctx, sizes, stream=None):
     ctx.check(lib().lp_autotune_batched_u64(ctx.h, arr, len(sizes), _stream(stream),
                                             C.byref(best)))
     return {"ctas": best.ctas, "line_bytes": best.line_bytes, "min_chunks": best.min_chunks,
-            "group_workers": best.group_workers, "min_chunks_residual": best.min_chunks_residual}
+            "group_workers": best.group_workers, "min_chunks_residual": best.min_chunks_residual,
+            "onchip_slices": best.onchip_slices}
 
 
 def lp_ctx_set_batch_tuning(ctx, ctas=0, line_bytes=0, min_chunks=0, group_workers=0,
-                            min_chunks_residual=0):
-    t = lp_batch_tuning(ctas, line_bytes, min_chunks, group_workers, min_chunks_residual)
+                            min_chunks_residual=0, onchip_slices=0):
+    t = lp_batch_tuning(ctas, line_bytes, min_chunks, group_workers, min_chunks_residual,
+                        onchip_slices)
     ctx.check(lib().lp_ctx_set_batch_tuning(ctx.h, C.byref(t)))
 
 

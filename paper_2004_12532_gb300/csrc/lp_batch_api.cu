@@ -35,6 +35,7 @@ lp::BatchTuning to_internal(const lp_batch_tuning& t) {
   b.line_bytes = t.line_bytes;
   b.min_chunks = t.min_chunks;
   b.min_chunks_residual = t.min_chunks_residual;
+  b.mc_slices = t.onchip_slices;
   return b;
 }
 
@@ -278,7 +279,7 @@ lp_status lp_autotune_batched_u64(lp_ctx* c, const uint64_t* sizes, uint32_t cou
   for (uint32_t lb : line_opts)
     for (uint32_t mc : chunk_opts)
       for (uint32_t ct : cta_opts) {
-        lp_batch_tuning t{ct, lb, mc, 0, 0};
+        lp_batch_tuning t{ct, lb, mc, 0, 0, 0};
         c->tuning = t;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 2 && st == LP_OK; rep++) {

@@ -9,17 +9,17 @@
 //         (its unaligned head and tail are put in place, the split written);
 //         a residual range (after the first step) that one CTA's shared
 //         memory holds becomes a CTA task (the base case, finished on chip);
-//         one that kMcMinSlices or more CTAs (up to the grid) hold becomes a
+//         one that more than one CTA (up to the grid) holds becomes a
 //         multi-CTA finish: that many CTAs stage a slice each, count, and
-//         after a grid barrier write a stable partition of the whole range;
+//         once all of the range is on chip write a stable partition of it;
 //         a first range of at most warp_cap keys gets a one-group step (g = 1:
 //         one warp partitions the whole range, as the paper's base case
 //         partitions serially); a larger one a step with g groups from the
 //         parameter rule.  Grid barrier; every CTA places its slice's tasks:
 //         CTA tasks and one-group segments in lists, multi-group segments
 //         with the prefix of their group counts.  Grid barrier.
-//   tasks the multi-CTA finishes run first, in windows of gridDim.x slices;
-//         every CTA takes CTA tasks from one counter; then every warp takes
+//   tasks the multi-CTA finishes run first, their slices taken in order from
+//         a counter; every CTA takes CTA tasks from another; then every warp takes
 //         warp tasks from another -- the groups of multi-group segments first
 //         (binary search over their prefix), then the one-group segments --
 //         and partitions that group (warp_pair_group, as in the single
@@ -166,16 +166,15 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
               d.g = 0;
               d.b = 1;
               in[3] = 1;
-            } else if (level > 0 && m >= (uint64_t)kMcMinSlices * cta_cap &&
-                       m <= (uint64_t)gridDim.x * cta_cap) {
-              // a residual range c CTAs hold (c >= kMcMinSlices: ranges that
-              // would take several more steps): finished on chip by c CTAs at
-              // once, a stable partition (the same as one CTA's); its keys
-              // are counted when it runs
+            } else if (level > 0 && m <= (uint64_t)a.mc_slices * cta_cap) {
+              // a residual range c > 1 CTAs hold: finished on
+              // chip by c CTAs, a stable partition (the same as one CTA's);
+              // its keys are counted when it runs
               const uint64_t c = (m + cta_cap - 1) / cta_cap;
               d.g = 0;
               d.b = c;
               d.t = 0ull;  // slices done
+              d.staged = 0u;
               in[4] = (uint32_t)c;
               in[5] = 1;
             } else {
@@ -284,6 +283,8 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
       B.mcprefix[n_mc] = n_mcslots;
       B.counters[0] = 0u;
       B.counters[1] = 0u;
+      B.counters[2] = 0u;
+      B.counters[3] = 0u;
       __threadfence();
     }
     if (!sync_grid()) return;
@@ -299,48 +300,95 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
       if (lane == 0)
         for (uint32_t st = 0; st < R::Stages; st++) mbar_inval(&ws.bar[st]);
       __syncthreads();
-      // multi-CTA finishes, in windows of gridDim.x slices: in a window
-      // starting at slice w0, CTA b stages and counts slice w0 + b if its
-      // finish [p, p + c) lies inside the window; after a grid barrier it
-      // writes its predecessors and successors to their final places, and
-      // the last slice of a finish to complete places the head and tail.  A
-      // finish cut by the window's end starts the next window.
-      for (uint32_t w0 = 0; w0 < n_mcslots;) {
-        auto finish_of = [&](uint32_t slot) {  // the last finish starting at or before slot
-          uint32_t lo_k = 0, hi_k = n_mc;
-          while (hi_k - lo_k > 1) {
-            const uint32_t mid = (lo_k + hi_k) >> 1;
-            if (__ldcg(&B.mcprefix[mid]) <= slot) lo_k = mid; else hi_k = mid;
-          }
-          return lo_k;
-        };
-        const uint32_t wend = w0 + gridDim.x;
-        const uint32_t slot = w0 + blockIdx.x;
-        uint32_t k = 0, p = 0, c = 0;
-        bool active = false;
-        if (slot < n_mcslots) {
-          k = finish_of(slot);
-          p = __ldcg(&B.mcprefix[k]);
-          c = __ldcg(&B.mcprefix[k + 1]) - p;
-          active = p >= w0 && (uint64_t)p + c <= wend;
+      // multi-CTA finishes.  CTAs take slices in slice order from a counter;
+      // each stages and counts its slice, adds it to its finish's staged
+      // count and waits until every slice of the finish is staged (all of the
+      // range's keys on chip); then it writes its predecessors and successors
+      // to their final places, and the last slice of a finish to complete
+      // places the head and tail.  A finish has at most gridDim.x slices and
+      // a CTA holds one slice at a time, taken in order, so the slices a CTA
+      // waits for are taken by CTAs that wait for nothing else: every wait
+      // ends.  The counts live in windows of a.mc_window slices (at least
+      // any finish's), grid barriers between; a finish cut by a window's end
+      // starts the next.
+      // the last finish starting at or before slot: a 32-way search, one
+      // probe per lane (the starts increase), a few dependent loads deep
+      auto finish_of = [&](uint32_t slot) {
+        uint32_t lo_k = 0, hi_k = n_mc;
+        while (hi_k - lo_k > 1) {
+          const uint32_t step = (hi_k - lo_k + 31) / 32;
+          const uint32_t q = lo_k + (lane + 1) * step;
+          const bool le = q < hi_k && __ldcg(&B.mcprefix[q]) <= slot;
+          const uint32_t below = __popc(__ballot_sync(0xffffffffu, le));
+          lo_k += below * step;
+          const uint32_t h = lo_k + step;
+          hi_k = h < hi_k ? h : hi_k;
         }
-        uint32_t got = 0, s = 0;
-        uint64_t lo = 0, m = 0, a0 = 0, nj = 0;
-        if (active) {
-          s = __ldcg(&B.mcseg[k]);
+        return lo_k;
+      };
+      uint32_t win = 0;
+      for (uint32_t w0 = 0; w0 < n_mcslots; win++) {
+        uint32_t wend = n_mcslots - w0 > a.mc_window ? w0 + a.mc_window : n_mcslots;
+        if (wend < n_mcslots) {
+          const uint32_t kc = finish_of(wend - 1);
+          const uint32_t pc = __ldcg(&B.mcprefix[kc]);
+          if (__ldcg(&B.mcprefix[kc + 1]) > wend) wend = pc;
+        }
+        if (wend <= w0) {  // a finish longer than a window: never planned, never run
+          if (tid == 0) atomicOr(S.status, kStatTimeout | kSiteRounds);
+          return;
+        }
+        uint32_t* const claim = &B.counters[2 + (win & 1u)];
+        // the next window's counter: every CTA took its last slice from it
+        // before the barrier that opened this window
+        if (blockIdx.x == 0 && tid == 0) B.counters[2 + ((win + 1u) & 1u)] = 0u;
+        for (;;) {
+          if (tid == 0) fetch = atomicAdd(claim, 1u);
+          __syncthreads();
+          const uint32_t slot = w0 + fetch;
+          __syncthreads();
+          if (slot >= wend) break;
+          const uint32_t k = finish_of(slot);
+          const uint32_t p = __ldcg(&B.mcprefix[k]);
+          const uint32_t c = __ldcg(&B.mcprefix[k + 1]) - p;
+          const uint32_t s = __ldcg(&B.mcseg[k]);
           SegDesc& d = segs[s];
-          lo = L2(d.lo);
-          m = L2(d.hi) - lo;
+          T* keys = reinterpret_cast<T*>(d.keys);
+          const T pivot = (T)L2(d.pivot);
+          const uint64_t lo = L2(d.lo), m = L2(d.hi) - lo;
           const uint64_t w = ((m + c - 1) / c + R::A - 1) / R::A * R::A;
-          a0 = min(m, (uint64_t)(slot - p) * w);
-          nj = min(m, a0 + w) - a0;
+          const uint64_t a0 = min(m, (uint64_t)(slot - p) * w);
+          const uint64_t nj = min(m, a0 + w) - a0;
+          uint32_t got = 0;
           if (nj > 0)
-            got = cta_bulk_stage<T>(reinterpret_cast<T*>(d.keys) + lo + a0, (uint32_t)nj,
-                                    (T)L2(d.pivot), smem_raw, &cta_bar, cta_parity, S.status);
-          if (tid == 0) B.mccount[slot - w0] = got == ~0u ? 0u : got;
-        }
-        if (!sync_grid()) return;
-        if (active && got != ~0u) {
+            got = cta_bulk_stage<T>(keys + lo + a0, (uint32_t)nj, pivot, smem_raw, &cta_bar,
+                                    cta_parity, S.status);
+          // publish the count, then wait for the finish's other slices
+          fence_proxy_async_global();
+          __syncthreads();
+          if (tid == 0) {
+            B.mccount[slot - w0] = got == ~0u ? 0u : got;
+            __threadfence();
+            atomicAdd(&d.staged, 1u);
+            bool ok = got != ~0u;
+            const volatile uint32_t* sv = &d.staged;
+            const uint64_t t0 = global_timer_ns();
+            while (*sv < c) {
+              if (global_timer_ns() - t0 > kWaitLimitNs) {
+                atomicOr(S.status, kStatTimeout | kSiteRounds);
+                ok = false;
+                break;
+              }
+              __nanosleep(32);
+            }
+            __threadfence();
+            // a slice that could not be staged leaves the finish unwritten
+            if (ok && (*reinterpret_cast<volatile uint32_t*>(S.status) & kStatTimeout)) ok = false;
+            flag = ok ? 1u : 0u;
+          }
+          __syncthreads();
+          fence_proxy_async_global();
+          if (!flag) break;
           // predecessors of the slices before this one, and of the whole range
           unsigned long long before = 0, all = 0;
           for (uint32_t q = tid; q < c; q += R::Threads) {
@@ -363,9 +411,6 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
             pb += wsum[0][w2];
             pt += wsum[1][w2];
           }
-          SegDesc& d = segs[s];
-          T* keys = reinterpret_cast<T*>(d.keys);
-          const T pivot = (T)L2(d.pivot);
           if (nj > 0)
             cta_bulk_scatter<T>(keys + lo + pb, keys + lo + pt + (a0 - pb), (uint32_t)nj, pivot,
                                 smem_raw);
@@ -374,34 +419,39 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
           if (tid == 0) {
             if (slot == p) atomicAdd(&B.totals[2], (unsigned long long)m);  // keys streamed
             if (atomicAdd(&d.t, 1ull) + 1 == c) {  // the last slice: the others' writes are visible
-              __threadfence();
-              const unsigned long long t =
-                  seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), L2(d.body_count), pivot);
-              d.t = t;
-              a.splits[s] = t;
-              d.state = kSegDone;
+              if (round < a.max_rounds) {  // the next plan places the head and tail
+                d.vmin = lo;
+                d.vmax = lo;
+              } else {
+                __threadfence();
+                const unsigned long long t =
+                    seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), L2(d.body_count), pivot);
+                d.t = t;
+                a.splits[s] = t;
+                d.state = kSegDone;
+              }
             }
           }
+          __syncthreads();
         }
-        __syncthreads();
-        // the next window: at the finish cut by this one's end, if any
-        uint32_t next = wend;
-        if (wend < n_mcslots) {
-          const uint32_t kc = finish_of(wend - 1);
-          const uint32_t pc = __ldcg(&B.mcprefix[kc]);
-          if (__ldcg(&B.mcprefix[kc + 1]) > wend) next = pc;
-        }
-        w0 = next;
-        // the next window's counts reuse B.mccount: every CTA has read this
-        // window's before any writes them again
+        w0 = wend;
         if (w0 < n_mcslots && !sync_grid()) return;
       }
+      // a residual range finished on chip leaves an empty open range: the
+      // next round's plan (one thread per segment) puts its head and tail in
+      // place and writes the split, off this CTA's path -- but not after the
+      // last round
+      const bool defer = round < a.max_rounds;
+      uint32_t next = 0;
+      if (tid == 0) next = atomicAdd(&B.counters[1], 1u);
       for (;;) {
-        if (tid == 0) fetch = atomicAdd(&B.counters[1], 1u);
+        if (tid == 0) fetch = next;
         __syncthreads();
         const uint32_t c = fetch;
         __syncthreads();
         if (c >= n_cta) break;
+        // the following task, taken now: the counter's latency hides behind this one
+        if (tid == 0) next = atomicAdd(&B.counters[1], 1u);
         const uint32_t s = __ldcg(&B.ctalist[c]);
         SegDesc& d = segs[s];
         T* keys = reinterpret_cast<T*>(d.keys);
@@ -411,13 +461,19 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
                                                    smem_raw, &cta_bar, cta_parity, S.status);
         if (cnt == ~0u) break;  // a wait gave up (status set)
         if (tid == 0) {
-          __threadfence_block();
-          // a first-level CTA task partitioned the whole body
-          const unsigned long long bc = L2(d.level) == 0 ? cnt : L2(d.body_count);
-          const unsigned long long t = seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), bc, pivot);
-          d.t = t;
-          a.splits[s] = t;
-          d.state = kSegDone;
+          if (defer && L2(d.level) > 0) {
+            d.vmin = lo;
+            d.vmax = lo;
+          } else {
+            __threadfence_block();
+            // a first-level CTA task partitioned the whole body
+            const unsigned long long bc = L2(d.level) == 0 ? cnt : L2(d.body_count);
+            const unsigned long long t =
+                seg_fixup<T>(keys, L2(d.n), L2(d.h), L2(d.be), bc, pivot);
+            d.t = t;
+            a.splits[s] = t;
+            d.state = kSegDone;
+          }
         }
         __syncthreads();
       }
@@ -519,7 +575,7 @@ size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 size_t batch_scratch_bytes(uint32_t count) {
   return up256(((size_t)count + 1) * 8) + 3 * up256((size_t)count * 4) +
          up256(((size_t)count + 1) * 4) + up256((size_t)count * 4) +
-         up256((size_t)kBatchMaxGrid * 4) + up256((size_t)kBatchMaxGrid * kPlanKinds * 4) +
+         up256((size_t)kMcWindow * 4) + up256((size_t)kBatchMaxGrid * kPlanKinds * 4) +
          up256(kBatchRoundSlots * 4 * 8) + 256;
 }
 
@@ -539,7 +595,7 @@ BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint
   B.mcseg = reinterpret_cast<uint32_t*>(p);
   p += up256((size_t)count * 4);
   B.mccount = reinterpret_cast<uint32_t*>(p);
-  p += up256((size_t)kBatchMaxGrid * 4);
+  p += up256((size_t)kMcWindow * 4);
   B.cta_tot = reinterpret_cast<uint32_t*>(p);
   p += up256((size_t)kBatchMaxGrid * kPlanKinds * 4);
   B.tround = reinterpret_cast<unsigned long long*>(p);
@@ -576,6 +632,8 @@ cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint6
   a.min_chunks = tune.min_chunks ? tune.min_chunks : 32;
   a.warp_cap = kWarpCapBytes / R::K;
   a.min_chunks_residual = tune.min_chunks_residual ? tune.min_chunks_residual : a.min_chunks;
+  a.mc_slices = tune.mc_slices && tune.mc_slices < grid ? tune.mc_slices : grid;
+  a.mc_window = a.mc_slices < grid ? 4 * a.mc_slices : kMcWindow;
   const size_t smem = level_smem_bytes<T, false>();  // attribute set by batched_prepare
   e = launch_cooperative(batched_kernel<T>, grid, R::Threads, smem, st, d_segs, count, a, Bs);
   cfg.launches++;

@@ -24,6 +24,8 @@ struct SegDesc {
   unsigned long long body_count;    // predecessors of the body (from level 0)
   unsigned long long t;             // the split, once done
   uint32_t level, state;
+  uint32_t staged;                  // multi-CTA finish: slices staged on chip so far
+  uint32_t spare;
 };
 
 // Open ranges of at most this many bytes get a one-group step: one warp
@@ -33,9 +35,10 @@ constexpr uint32_t kWarpCapBytes = 128u * 1024u;
 constexpr uint32_t kBatchMaxGrid = 1024;
 // task kinds a plan counts per CTA
 constexpr uint32_t kPlanKinds = 6;
-// residual ranges of at least this many CTAs' shared memory (and at most the
-// grid's) are finished on chip by that many CTAs at once
-constexpr uint32_t kMcMinSlices = 16;
+// slices of multi-CTA finishes per window (their counts' space); a grid
+// barrier separates windows
+constexpr uint32_t kMcWindow = 16384;
+static_assert(kMcWindow >= 4 * kBatchMaxGrid, "a window holds any finish");
 // rounds recorded in BatchScratch::tround
 constexpr uint32_t kBatchRoundSlots = 12;
 
@@ -47,6 +50,8 @@ struct BatchArgs {
   uint32_t min_chunks;    // lines per group, at least
   uint64_t warp_cap;      // one-group steps for open ranges of at most this many keys
   uint32_t min_chunks_residual;  // lines per group, at least, after the first step
+  uint32_t mc_slices;     // multi-CTA finishes span at most this many slices (<= grid)
+  uint32_t mc_window;     // slices per window of their counts (>= mc_slices)
 };
 
 struct BatchScratch {
@@ -56,12 +61,12 @@ struct BatchScratch {
   uint32_t* ctalist;            // CTA-task segments: ids
   uint32_t* mcprefix;           // multi-CTA finishes: prefix of their CTA slices
   uint32_t* mcseg;              // multi-CTA finishes: ids
-  uint32_t* mccount;            // per CTA slice: its predecessor count
+  uint32_t* mccount;            // per slice of a window: its predecessor count
   uint32_t* cta_tot;            // per CTA: singles, groups, multi-group segments, CTA tasks,
                                 // multi-CTA slices, multi-CTA segments
   unsigned long long* totals;   // [2]: keys streamed
   unsigned long long* tround;   // per round: plan start, tasks start, tasks end (ns), tasks
-  uint32_t* counters;           // task fetch counter
+  uint32_t* counters;           // task fetch counters: warp tasks, CTA tasks, slices (2)
   uint32_t* bar;                // grid barrier
   uint32_t* status;
 };
@@ -73,6 +78,8 @@ struct BatchTuning {
   uint32_t line_bytes;     // 128..1024
   uint32_t min_chunks;     // lines per group, at least
   uint32_t min_chunks_residual;  // ... in steps after the first
+  uint32_t mc_slices;      // multi-CTA finishes span at most this many slices; below the
+                           // grid it also cuts their windows to 4x that (tests)
 };
 
 size_t batch_scratch_bytes(uint32_t count);

@@ -33,7 +33,7 @@ struct lp_ctx {
   size_t batch_bytes = 0;
   void* h_batch = nullptr;
   size_t h_batch_bytes = 0;
-  lp_batch_tuning tuning{0, 0, 0, 0, 0};
+  lp_batch_tuning tuning{0, 0, 0, 0, 0, 0};
   unsigned long long* last_batch_traffic = nullptr;  // streamed-keys counter of the last batch
   unsigned long long* last_batch_tround = nullptr;   // its round timestamps
   lp_sort_stats sort_stats{};                         // of the last quicksort

@@ -257,6 +257,7 @@ cudaError_t run_width(lp_server* s, int k, uint32_t nparts, uint32_t njobs, uint
   tune.min_chunks = s->ctx->tuning.min_chunks;
   tune.group_workers = s->ctx->tuning.group_workers;
   tune.min_chunks_residual = s->ctx->tuning.min_chunks_residual;
+  tune.mc_slices = s->ctx->tuning.onchip_slices;
   if (tune.ctas && tune.ctas < cfg.grid) cfg.grid = tune.ctas;
   cudaError_t e = cudaSuccess;
   if (njobs > 0 && max_open > 0) {

@@ -183,32 +183,61 @@ def test_residual_tuning_keeps_results_valid(ctx, mcr):
         lp.lp_ctx_set_batch_tuning(ctx)
 
 
-def test_multi_cta_finish_same_in_any_batch(ctx):
-    """Segments large enough that their first step leaves open ranges of 16
-    or more CTAs' shared memory, which several CTAs finish on chip at once,
-    and enough of them that the slices take several windows of the grid: each
-    result equals the oracle's, and is byte for byte the result of the same
-    segment at the same place in a batch of its own."""
+@pytest.mark.parametrize("onchip_slices", [0, 4])
+def test_multi_cta_finish_same_in_any_batch(ctx, onchip_slices):
+    """Segments large enough that their first step leaves open ranges of
+    several CTAs' shared memory, which several CTAs finish on chip at once
+    (each slice waits for the others of its range to be staged): each result
+    equals the oracle's, and is byte for byte the result of the same segment
+    at the same place in a batch of its own.  At most 4 slices per range cut
+    the windows of their counts to 16 slices, so the finishes take several
+    windows."""
     sizes = [(1 << 24) + 3] * 3 + [(1 << 23) + 1001] * 4 + [5000, 70001]
     host, offs, pivots = make_batch(sizes, 99)
-    buf = to_dev(host)
-    views = [buf[o:o + n] for o, n in zip(offs, sizes)]
-    splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
-    lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=6)
-    torch.cuda.synchronize()
-    out = to_host(buf, np.uint64)
-    check_batch(out, host, offs, sizes, pivots, splits.cpu().numpy())
-    for s in (0, 4):
-        o, n = offs[s], sizes[s]
-        # the same offset modulo 16 bytes as in the batch buffer, so the
-        # same unaligned head and body
-        k = o % 2
-        whole = to_dev(host[o - k:o + n])
-        alone = whole[k:]
-        empty = whole[0:0]
-        sp = torch.zeros(s + 1, dtype=torch.int64, device="cuda")
-        lp.lp_partition_batched_u64(ctx, [empty] * s + [alone], [0] * s + [pivots[s]], sp,
-                                    seed=6)
+    lp.lp_ctx_set_batch_tuning(ctx, onchip_slices=onchip_slices)
+    try:
+        buf = to_dev(host)
+        views = [buf[o:o + n] for o, n in zip(offs, sizes)]
+        splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+        lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=6)
         torch.cuda.synchronize()
-        assert int(sp[s].item()) == int(splits[s].item())
-        assert np.array_equal(to_host(alone, np.uint64), out[o:o + n])
+        out = to_host(buf, np.uint64)
+        check_batch(out, host, offs, sizes, pivots, splits.cpu().numpy())
+        for s in (0, 4):
+            o, n = offs[s], sizes[s]
+            # the same offset modulo 16 bytes as in the batch buffer, so the
+            # same unaligned head and body
+            k = o % 2
+            whole = to_dev(host[o - k:o + n])
+            alone = whole[k:]
+            empty = whole[0:0]
+            sp = torch.zeros(s + 1, dtype=torch.int64, device="cuda")
+            lp.lp_partition_batched_u64(ctx, [empty] * s + [alone], [0] * s + [pivots[s]], sp,
+                                        seed=6)
+            torch.cuda.synchronize()
+            assert int(sp[s].item()) == int(splits[s].item())
+            assert np.array_equal(to_host(alone, np.uint64), out[o:o + n])
+    finally:
+        lp.lp_ctx_set_batch_tuning(ctx)
+
+
+def test_many_multi_cta_finishes_in_one_round(ctx):
+    """Forty segments of about 2^20 keys: their first steps leave residual
+    ranges of a few CTAs' shared memory each, all finished on chip in the same
+    round by CTAs that take their slices from one counter; with at most 3
+    slices per range (windows of 12 slices) the same batch runs through many
+    windows.  Both give oracle-exact splits and sides."""
+    sizes = [(1 << 20) + 17 * i for i in range(40)]
+    host, offs, pivots = make_batch(sizes, 123)
+    for slices in (0, 3):
+        lp.lp_ctx_set_batch_tuning(ctx, onchip_slices=slices)
+        try:
+            buf = to_dev(host)
+            views = [buf[o:o + n] for o, n in zip(offs, sizes)]
+            splits = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+            lp.lp_partition_batched_u64(ctx, views, pivots, splits, seed=11)
+            torch.cuda.synchronize()
+            check_batch(to_host(buf, np.uint64), host, offs, sizes, pivots,
+                        splits.cpu().numpy())
+        finally:
+            lp.lp_ctx_set_batch_tuning(ctx)
