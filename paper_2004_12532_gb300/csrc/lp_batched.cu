@@ -24,7 +24,9 @@
 //         (binary search over their prefix), then the one-group segments --
 //         and partitions that group (warp_pair_group, as in the single
 //         partition); v_i go to the segment's record by atomic min / max.
-//         Grid barrier.
+//         Grid barrier.  A round whose tasks were all on-chip finishes is
+//         the last: each CTA then places the heads and tails of its slice's
+//         segments itself.
 // A segment's steps depend on its own size and state only (never on what it
 // is batched with), so its result is the same in any batch.
 #include <cuda_runtime.h>
@@ -524,6 +526,22 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
     __syncwarp();
     if (!sync_grid()) return;
     if (stamp && tr) tr[2] = global_timer_ns();
+    if (n_single == 0 && w_multi == 0) {
+      // only on-chip finishes ran: every segment still open has an empty open
+      // range, so what a further plan would do is this -- its head and tail
+      // put in place, its split written -- with no grid barrier after it
+      for (uint32_t s = s_lo + tid; s < s_hi; s += R::Threads) {
+        SegDesc& d = segs[s];
+        if (L2(d.state) != kSegOpen) continue;
+        const unsigned long long t =
+            seg_fixup<T>(reinterpret_cast<T*>(d.keys), L2(d.n), L2(d.h), L2(d.be),
+                         L2(d.body_count), (T)L2(d.pivot));
+        d.t = t;
+        a.splits[s] = t;
+        d.state = kSegDone;
+      }
+      break;
+    }
   }
   __syncthreads();
   if (lane == 0) {
