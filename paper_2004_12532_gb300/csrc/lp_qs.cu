@@ -33,15 +33,39 @@ __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const ui
   qs_item_children(J, J.items[i], splits[J.seg_base + i], segs[J.seg_base + i].pivot);
 }
 
+// The bucket sort of every small subarray; those whose keys bunch go to the
+// job's merge list.  Without the merge sort's code the kernel fits 64
+// registers a thread: 4 CTAs per SM keep more subarrays' loads in flight than
+// 3 did with both sorts in one kernel.
 template <typename T>
-__global__ void __launch_bounds__(kQsSortThreads, 3) qs_small_sort_kernel(const QsJob* jobs) {
+__global__ void __launch_bounds__(kQsSortThreads, 4) qs_small_sort_kernel(const QsJob* jobs) {
   extern __shared__ __align__(16) unsigned char qs_smem[];
   const QsJob& J = jobs[blockIdx.y];
   const uint32_t cnt = *reinterpret_cast<volatile uint32_t*>(&J.lc->small);
   T* keys = static_cast<T*>(J.keys);
   for (uint32_t s = blockIdx.x; s < cnt; s += gridDim.x) {
     const QsSmall q = J.small[s];
-    cta_sort_small<T>(keys + q.lo, (uint32_t)q.n, qs_smem);
+    const uint32_t n = (uint32_t)q.n;
+    if (n < 2) continue;
+    T x[kE];
+    cta_load_small<T>(keys + q.lo, n, x);
+    if (!cta_bucket_sort<T>(keys + q.lo, n, x, qs_smem) && threadIdx.x == 0)
+      J.merge[atomicAdd(&J.lc->merge, 1u)] = s;
+  }
+}
+
+// The merge sort of the subarrays the bucket sort listed.
+template <typename T>
+__global__ void __launch_bounds__(kQsSortThreads, 3) qs_merge_sort_kernel(const QsJob* jobs) {
+  extern __shared__ __align__(16) unsigned char qs_smem[];
+  const QsJob& J = jobs[blockIdx.y];
+  const uint32_t cnt = *reinterpret_cast<volatile uint32_t*>(&J.lc->merge);
+  T* keys = static_cast<T*>(J.keys);
+  for (uint32_t k = blockIdx.x; k < cnt; k += gridDim.x) {
+    const QsSmall q = J.small[J.merge[k]];
+    T x[kE];
+    cta_load_small<T>(keys + q.lo, (uint32_t)q.n, x);
+    cta_merge_sort<T>(keys + q.lo, (uint32_t)q.n, x, qs_smem);
   }
 }
 
@@ -69,18 +93,36 @@ template <typename T>
 cudaError_t launch_qs_small_sort(const QsJob* jobs, uint32_t njobs, uint32_t ctas,
                                  cudaStream_t st) {
   if (njobs == 0 || ctas == 0) return cudaSuccess;
-  qs_small_sort_kernel<T><<<dim3(ctas, njobs), kQsSortThreads, SortSmem<T>::kBytes, st>>>(jobs);
+  qs_small_sort_kernel<T><<<dim3(ctas, njobs), kQsSortThreads, SortSmem<T>::kBucketBytes, st>>>(
+      jobs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_qs_merge_sort(const QsJob* jobs, uint32_t njobs, uint32_t ctas,
+                                 cudaStream_t st) {
+  if (njobs == 0 || ctas == 0) return cudaSuccess;
+  qs_merge_sort_kernel<T><<<dim3(ctas, njobs), kQsSortThreads, SortSmem<T>::kMergeBytes, st>>>(
+      jobs);
   return cudaGetLastError();
 }
 
 cudaError_t qs_prepare() {
   cudaError_t e = cudaFuncSetAttribute(qs_small_sort_kernel<uint64_t>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SortSmem<uint64_t>::kBytes);
+                                       (int)SortSmem<uint64_t>::kBucketBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(qs_small_sort_kernel<uint32_t>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SortSmem<uint32_t>::kBytes);
+                             (int)SortSmem<uint32_t>::kBucketBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(qs_merge_sort_kernel<uint64_t>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SortSmem<uint64_t>::kMergeBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(qs_merge_sort_kernel<uint32_t>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SortSmem<uint32_t>::kMergeBytes);
   return e;
 }
 
@@ -91,6 +133,10 @@ template cudaError_t launch_qs_build<uint32_t>(const QsJob*, uint32_t, uint32_t,
 template cudaError_t launch_qs_small_sort<uint64_t>(const QsJob*, uint32_t, uint32_t,
                                                     cudaStream_t);
 template cudaError_t launch_qs_small_sort<uint32_t>(const QsJob*, uint32_t, uint32_t,
+                                                    cudaStream_t);
+template cudaError_t launch_qs_merge_sort<uint64_t>(const QsJob*, uint32_t, uint32_t,
+                                                    cudaStream_t);
+template cudaError_t launch_qs_merge_sort<uint32_t>(const QsJob*, uint32_t, uint32_t,
                                                     cudaStream_t);
 
 }  // namespace lp

@@ -41,7 +41,7 @@ struct QsSmall {
 struct QsLevelCounts {
   uint32_t next, small;
   uint32_t max_next;  // keys of the largest item of the next list (saturated at 2^32 - 1)
-  uint32_t pad;
+  uint32_t merge;     // small subarrays the bucket sort left to the merge sort
 };
 
 // One slice of one job's list in one launch.
@@ -50,6 +50,8 @@ struct QsJob {
   const QsItem* items;             // this slice of the level's list
   QsItem* next;                    // the next level's list (whole job)
   QsSmall* small;                  // the level's small list (whole job)
+  uint32_t* merge;                 // indices into it: the merge sort's subarrays (room
+                                   // for as many entries as the small list)
   QsLevelCounts* lc;               // the job's level counts
   unsigned long long* sort_keys;   // keys the job sorted in shared memory, accumulated
   uint64_t seed;                   // the job's seed (pivots and offsets X)
@@ -74,9 +76,17 @@ cudaError_t launch_qs_split(const QsJob* jobs, uint32_t njobs, uint32_t max_coun
                             const unsigned long long* traffic, unsigned long long* traffic_acc,
                             cudaStream_t st);
 
-// Sorts every job's small list in shared memory; `ctas` CTAs per job.
+// Sorts every job's small list in shared memory; `ctas` CTAs per job.  The
+// bucket sort runs here (4 CTAs per SM); a subarray whose keys bunch goes to
+// the job's merge list instead, counted in lc->merge, and stays unsorted
+// until launch_qs_merge_sort -- which the caller runs, when a read-back shows
+// a nonzero count, before the lists are reused.
 template <typename T>
 cudaError_t launch_qs_small_sort(const QsJob* jobs, uint32_t njobs, uint32_t ctas,
+                                 cudaStream_t st);
+// The merge sort of every job's merge list.
+template <typename T>
+cudaError_t launch_qs_merge_sort(const QsJob* jobs, uint32_t njobs, uint32_t ctas,
                                  cudaStream_t st);
 
 // Sets the shared-memory attribute of the sort kernels (once per device).

@@ -142,11 +142,15 @@ __device__ __forceinline__ uint32_t cta_scan_u32(uint32_t v, uint32_t* ws, uint3
   return before + incl - v;
 }
 
-// Sorts keys[0..n), n <= kQsCut, ascending, with all kQsSortThreads threads of
-// the CTA (blockDim.x == kQsSortThreads); `smem` holds SortSmem<T>::kBytes.
-// Ends with a CTA barrier (the buffer may be reused at once).
+// The sort of keys[0..n), n <= kQsCut, ascending, by all kQsSortThreads
+// threads of the CTA (blockDim.x == kQsSortThreads), `smem` holding
+// SortSmem<T>::kBytes: a load into registers, then the bucket sort, and the
+// merge sort for the subarrays the bucket sort turns down.  Each part ends
+// with a CTA barrier (the buffer may be reused at once); cta_sort_small runs
+// all three, and the quicksort's levels run the merge sort in a kernel of its
+// own, so that the bucket sort's kernel needs fewer registers.
 //
-// First a bucket sort: with [lo, hi] the keys' range, key x goes to bucket
+// The bucket sort: with [lo, hi] the keys' range, key x goes to bucket
 // (x - lo) >> s, s chosen so that at most kQsCut / 2 (about n / 2) buckets are
 // used -- a monotone map, so the buckets in order are the sorted order up to
 // the order inside each bucket.  A histogram, its scan and a scatter by
@@ -157,19 +161,11 @@ __device__ __forceinline__ uint32_t cta_scan_u32(uint32_t v, uint32_t* ws, uint3
 // kBucketSortMax, the subarray is merge sorted instead (below).  All keys
 // equal: nothing to do.
 template <typename T>
-__device__ __forceinline__ void cta_sort_small(T* __restrict__ keys, uint32_t n, unsigned char* smem) {
-  using S = SortSmem<T>;
-  T* const buf = reinterpret_cast<T*>(smem);
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  constexpr uint32_t kRun = 32 * kE;  // keys one warp sorts in registers
+__device__ __forceinline__ void cta_load_small(const T* __restrict__ keys, uint32_t n, T (&x)[kE]) {
+  // coalesced load through L2, every load issued before the first use; the
+  // positions past n hold the largest key
+  const uint32_t tid = threadIdx.x;
   const T big = (T)~(T)0;
-  if (n < 2) {
-    __syncthreads();
-    return;
-  }
-  // coalesced load through L2, every load issued before the first use
-  T x[kE];
-  T kmin = big, kmax = 0;
 #pragma unroll
   for (uint32_t m = 0; m < kE; m++) {
     const uint32_t i = tid + m * kQsSortThreads;
@@ -178,6 +174,20 @@ __device__ __forceinline__ void cta_sort_small(T* __restrict__ keys, uint32_t n,
     else
       x[m] = i < n ? (T)__ldcg(reinterpret_cast<const unsigned int*>(keys + i)) : big;
   }
+}
+
+// The bucket sort of keys[0..n) (2 <= n <= kQsCut) held in x as
+// cta_load_small leaves them.  Returns true (CTA-uniform) once keys[0..n) is
+// sorted, false -- keys untouched -- when a bucket holds more than
+// kBucketSortMax keys (the merge sort's case).  Ends with a CTA barrier.
+template <typename T>
+__device__ __forceinline__ bool cta_bucket_sort(T* __restrict__ keys, uint32_t n,
+                                                const T (&x)[kE], unsigned char* smem) {
+  using S = SortSmem<T>;
+  T* const buf = reinterpret_cast<T*>(smem);
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const T big = (T)~(T)0;
+  T kmin = big, kmax = 0;
 #pragma unroll
   for (uint32_t m = 0; m < kE; m++) {
     if (tid + m * kQsSortThreads < n) {
@@ -206,7 +216,7 @@ __device__ __forceinline__ void cta_sort_small(T* __restrict__ keys, uint32_t n,
     }
     __syncthreads();
   }
-  if (kmin == kmax) return;  // all keys equal (the barrier above ends the call)
+  if (kmin == kmax) return true;  // all keys equal (the barrier above ends the call)
   const T range = kmax - kmin;
   const uint32_t bits = sizeof(T) == 8 ? 64u - (uint32_t)__clzll((long long)range)
                                        : 32u - (uint32_t)__clz((int)range);
@@ -279,11 +289,23 @@ __device__ __forceinline__ void cta_sort_small(T* __restrict__ keys, uint32_t n,
         if (i < n) keys[i] = buf[i];
       }
       __syncthreads();
-      return;
+      return true;
     }
     __syncthreads();  // every thread has decided before the buffer is reused
   }
-  // the merge sort
+  return false;
+}
+
+// The merge sort of keys[0..n) (2 <= n <= kQsCut) held in x as cta_load_small
+// leaves them.  Ends with a CTA barrier.
+template <typename T>
+__device__ __forceinline__ void cta_merge_sort(T* __restrict__ keys, uint32_t n, const T (&x)[kE],
+                                               unsigned char* smem) {
+  using S = SortSmem<T>;
+  T* const buf = reinterpret_cast<T*>(smem);
+  const uint32_t tid = threadIdx.x;
+  constexpr uint32_t kRun = 32 * kE;  // keys one warp sorts in registers
+  const T big = (T)~(T)0;
   const uint32_t n16 = (n + kE - 1) / kE * kE;
   const uint32_t nrun = (n + kRun - 1) / kRun * kRun;  // whole warps' runs, padded
   const uint32_t d0 = tid * kE;  // this thread's first output position
@@ -347,6 +369,19 @@ __device__ __forceinline__ void cta_sort_small(T* __restrict__ keys, uint32_t n,
     if (i < n) keys[i] = buf[S::pad(i)];
   }
   __syncthreads();
+}
+
+// Sorts keys[0..n), n <= kQsCut: the bucket sort, else the merge sort.  Ends
+// with a CTA barrier.
+template <typename T>
+__device__ __forceinline__ void cta_sort_small(T* __restrict__ keys, uint32_t n, unsigned char* smem) {
+  if (n < 2) {
+    __syncthreads();
+    return;
+  }
+  T x[kE];
+  cta_load_small<T>(keys, n, x);
+  if (!cta_bucket_sort<T>(keys, n, x, smem)) cta_merge_sort<T>(keys, n, x, smem);
 }
 
 }  // namespace lp

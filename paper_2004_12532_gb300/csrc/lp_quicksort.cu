@@ -8,10 +8,12 @@
 // Per level: build the segment records (median-of-3 or -15 pivots), one batched
 // launch per slice of at most kSlice subarrays, split into children, sort the
 // level's small subarrays, read the next list's size back (one host
-// synchronisation per level).  Auxiliary memory: two item lists of at most
-// n / (kQsCut + 1) items (32 bytes each), a small list of twice that (16
-// bytes each), and the records of one slice of at most kSlice items (about
-// 2.9 MB) -- about 0.4% of a uint64 array's bytes at n = 2^28.
+// synchronisation per level), and merge sort the small subarrays the bucket
+// sort turned down, if it turned any down.  Auxiliary memory: two item lists
+// of at most n / (kQsCut + 1) items (32 bytes each), a small list of twice
+// that (16 bytes each) with a merge list beside it (4 bytes each), and the
+// records of one slice of at most kSlice items (about 2.9 MB) -- about 0.4%
+// of a uint64 array's bytes at n = 2^28.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +31,7 @@ constexpr uint32_t kMaxSortLevels = 4096;
 struct QsLayout {
   QsItem* lists[2];
   QsSmall* small;
+  uint32_t* merge;
   SegDesc* segs;
   uint64_t* splits;
   QsJob* jobs;                      // one record per slice
@@ -56,6 +59,7 @@ QsLayout qs_layout(void* base, uint64_t n) {
   L.lists[0] = reinterpret_cast<QsItem*>(take(L.maxseg * sizeof(QsItem)));
   L.lists[1] = reinterpret_cast<QsItem*>(take(L.maxseg * sizeof(QsItem)));
   L.small = reinterpret_cast<QsSmall*>(take(2 * L.maxseg * sizeof(QsSmall)));
+  L.merge = reinterpret_cast<uint32_t*>(take(2 * L.maxseg * sizeof(uint32_t)));
   L.segs = reinterpret_cast<SegDesc*>(take((size_t)L.slice * sizeof(SegDesc)));
   L.splits = reinterpret_cast<uint64_t*>(take((size_t)L.slice * 8));
   L.jobs = reinterpret_cast<QsJob*>(take((size_t)L.max_slices * sizeof(QsJob)));
@@ -125,6 +129,7 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
       J.items = L.lists[cur] + o;
       J.next = L.lists[cur ^ 1];
       J.small = L.small;
+      J.merge = L.merge;
       J.lc = L.lc;
       J.sort_keys = L.acc + 1;
       J.seed = seed;
@@ -162,6 +167,16 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
     if (e != cudaSuccess) return e;
     elapsed(0, 1, &stats->partition_ms);
     elapsed(1, 2, &stats->sort_ms);
+    const uint32_t merges = reinterpret_cast<const QsLevelCounts*>(hback)->merge;
+    if (merges > 0) {  // before the next level reuses the lists
+      if ((e = mark(1)) != cudaSuccess) return e;
+      e = launch_qs_merge_sort<T>(L.jobs, 1, merges < 2048 ? merges : 2048, st);
+      if (e != cudaSuccess) return e;
+      cfg.launches++;
+      if ((e = mark(2)) != cudaSuccess) return e;
+      if (ev && (e = cudaEventSynchronize(ev[2])) != cudaSuccess) return e;
+      elapsed(1, 2, &stats->sort_ms);
+    }
     if (nslices == 0) break;  // the small-only first level is done
     levels++;
     open = reinterpret_cast<const QsLevelCounts*>(hback)->next;

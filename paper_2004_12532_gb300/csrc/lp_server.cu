@@ -83,6 +83,7 @@ struct Req {
   // sort state
   QsItem* lists[2] = {nullptr, nullptr};
   QsSmall* small = nullptr;
+  uint32_t* merge = nullptr;   // the merge sort's indices into the small list
   uint32_t cur = 0, level = 0, slot = 0;
   uint64_t open = 0;
   uint64_t peak_open = 0;      // most open items any level of the sort held
@@ -98,13 +99,16 @@ uint64_t max_items(uint64_t n) { return n / (lp::kQsCut + 1) + 1; }
 uint64_t sort_list_bytes(uint64_t n) {
   if (n <= lp::kQsCut) return 0;
   return 2 * lp::Arena::rounded(max_items(n) * sizeof(QsItem)) +
-         lp::Arena::rounded(2 * max_items(n) * sizeof(QsSmall));
+         lp::Arena::rounded(2 * max_items(n) * sizeof(QsSmall)) +
+         lp::Arena::rounded(2 * max_items(n) * sizeof(uint32_t));
 }
 
 uint64_t request_bytes(const lp_request& r) {
   const uint64_t keys = lp::Arena::rounded(r.n * (r.key_bits / 8));
   return keys + (r.kind == LP_REQ_SORT ? sort_list_bytes(r.n) : 0) +
-         (r.kind == LP_REQ_SORT && r.n <= lp::kQsCut ? lp::Arena::rounded(sizeof(QsSmall)) : 0);
+         (r.kind == LP_REQ_SORT && r.n <= lp::kQsCut
+              ? lp::Arena::rounded(sizeof(QsSmall)) + lp::Arena::rounded(sizeof(uint32_t))
+              : 0);
 }
 
 // Device and pinned buffers of one key width.
@@ -325,11 +329,14 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
         q.lists[0] = reinterpret_cast<QsItem*>(p);
         q.lists[1] = reinterpret_cast<QsItem*>(p + lp::Arena::rounded(m * sizeof(QsItem)));
         q.small = reinterpret_cast<QsSmall*>(p + 2 * lp::Arena::rounded(m * sizeof(QsItem)));
+        q.merge = reinterpret_cast<uint32_t*>(p + 2 * lp::Arena::rounded(m * sizeof(QsItem)) +
+                                              lp::Arena::rounded(2 * m * sizeof(QsSmall)));
         q.open = 1;
         q.peak_open = 1;
         q.max_next = q.r.n;
       } else {
         q.small = reinterpret_cast<QsSmall*>(p);
+        q.merge = reinterpret_cast<uint32_t*>(p + lp::Arena::rounded(sizeof(QsSmall)));
         q.open = 0;
       }
     }
@@ -401,6 +408,7 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
     J.items = q.lists[q.cur];
     J.next = q.lists[q.cur ^ 1];
     J.small = q.small;
+    J.merge = q.merge;
     J.lc = s->d_lc + q.slot;
     J.sort_keys = s->d_sorted + q.slot;
     J.seed = q.r.seed;
@@ -484,6 +492,24 @@ lp_status engine_step(lp_server* s, uint32_t* in_flight) {
     return srv_fail(s, timeout ? LP_ERR_TIMEOUT : LP_ERR_INTERNAL,
                     timeout ? lp_timeout_what(dev_status) : "device status after an engine step");
   }
+  // small subarrays the bucket sort turned down: merge sorted before any
+  // result counts as done or any list is reused
+  bool merged = false;
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    uint32_t most = 0;
+    for (uint64_t id : job_ids[k]) {
+      const uint32_t m = S.lc_back[s->reqs[id].slot].merge;
+      most = m > most ? m : most;
+    }
+    if (most == 0) continue;
+    const uint32_t ctas = most < 2048 ? most : 2048;
+    e = k == 0 ? lp::launch_qs_merge_sort<uint64_t>(s->w[0].jobs, njobs[0], ctas, st)
+               : lp::launch_qs_merge_sort<uint32_t>(s->w[1].jobs, njobs[1], ctas, st);
+    s->stats.launches++;
+    merged = true;
+  }
+  if (e == cudaSuccess && merged) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return srv_cuda(s, e, "merge sort");
   s->stats.steps++;
   for (int k = 0; k < 2; k++) {
     float ms = 0.f;

@@ -35,6 +35,9 @@ def make(kind, n, seed, dtype=np.uint64):
             return inputs.uniform_u32(n, seed)
         if kind == "dup16":
             return (inputs.uniform_u32(n, seed) & np.uint32(15)).astype(np.uint32)
+        if kind == "bunched":
+            u = inputs.uniform_u32(n, seed)
+            return np.where((u >> 28) == 0, u, u & np.uint32(0xFFF)).astype(np.uint32)
         raise ValueError(kind)
     if kind == "uniform":
         return inputs.uniform_u64(n, seed)
@@ -50,6 +53,12 @@ def make(kind, n, seed, dtype=np.uint64):
         return np.zeros(n, dtype=np.uint64)
     if kind == "max":
         return np.full(n, np.uint64(2**64 - 1), dtype=np.uint64)
+    if kind == "bunched":
+        # 15 of 16 keys in [0, 4096), the rest anywhere: a small subarray that
+        # holds both has one bucket of most of its keys, so the bucket sort
+        # turns it down and the merge sort takes it
+        u = inputs.uniform_u64(n, seed)
+        return np.where((u >> 60) == 0, u, u & np.uint64(0xFFF)).astype(np.uint64)
     if kind == "two":
         return np.where(inputs.uniform_u64(n, seed) & np.uint64(1), np.uint64(0),
                         np.uint64(2**64 - 1)).astype(np.uint64)
@@ -79,13 +88,14 @@ def test_uniform_u64_sizes(ctx, n):
     run_and_compare(ctx, make("uniform", n, 100 + n))
 
 
-@pytest.mark.parametrize("kind", ["sorted", "reverse", "dup16", "equal", "zeros", "max", "two"])
+@pytest.mark.parametrize("kind", ["sorted", "reverse", "dup16", "equal", "zeros", "max", "two",
+                                  "bunched"])
 @pytest.mark.parametrize("n", [5000, 50001, 300000])
 def test_patterns_u64(ctx, kind, n):
     run_and_compare(ctx, make(kind, n, 7 + n))
 
 
-@pytest.mark.parametrize("kind", ["uniform", "dup16"])
+@pytest.mark.parametrize("kind", ["uniform", "dup16", "bunched"])
 @pytest.mark.parametrize("n", [1, 4096, 4097, 30001, 65536, 65537, 100003, 1 << 20, 1 << 25])
 def test_u32(ctx, kind, n):
     # 2^25 keys: the first levels leave open ranges that several CTAs finish

@@ -43,6 +43,9 @@ def mixed_requests(seed, count=40):
         keys = host_keys(n, bits, 1000 + i)
         if bits == 32 and kind == S and i % 3 == 0:
             keys = keys & np.uint32(15)  # heavy duplicates
+        if bits == 64 and kind == S and i % 3 == 1:
+            # 15 of 16 keys in [0, 4096): small subarrays the merge sort takes
+            keys = np.where((keys >> 60) == 0, keys, keys & np.uint64(0xFFF)).astype(np.uint64)
         pivot = int(keys[rng.integers(0, n)]) if n else 0
         reqs.append((kind, bits, n, pivot, 5000 + i, keys))
     return reqs
