@@ -49,8 +49,8 @@ HANDOFF = (1 << 64) - 1  # level record of a range handed to the low-space parti
 # summary feeds roofline.traffic only while the hash of these files matches.
 PART_SOURCES = ["lp_smoothed.cuh", "lp_kernels.cu", "lp_plan.h", "lp_device.cuh",
                 "lp_coop.cuh", "lp_launch.h"]
-BATCH_SOURCES = ["lp_batched.cu", "lp_batched.h", "lp_smoothed.cuh", "lp_plan.h",
-                 "lp_device.cuh", "lp_coop.cuh", "lp_fixup.cuh"]
+BATCH_SOURCES = ["lp_batched.cu", "lp_batched.h", "lp_batch_init.cuh", "lp_smoothed.cuh",
+                 "lp_plan.h", "lp_device.cuh", "lp_coop.cuh", "lp_fixup.cuh"]
 QS_SOURCES = BATCH_SOURCES + ["lp_qs.cu", "lp_qs.cuh", "lp_qs_sort.cuh", "lp_qs_pivot.cuh",
                               "lp_qs_level.cuh", "lp_qs_local.cu", "lp_quicksort.cu"]
 # name -> (summary file, kernel sources, machine-readable key of its DRAM bytes per unit)

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lp_batch_init.cuh"
 #include "lp_batched.h"
 #include "lp_coop.cuh"
 #include "lp_fixup.cuh"
@@ -40,8 +41,6 @@
 namespace lp {
 
 namespace {
-
-enum : uint32_t { kSegOpen = 0, kSegDone = 2 };
 
 // Segment fields written by other CTAs are read through L2, never from L1.
 __device__ __forceinline__ uint64_t L2(const uint64_t& x) {
@@ -556,32 +555,9 @@ __global__ void batch_setup_kernel(SegDesc* segs, uint32_t count, uint64_t seed,
                                    unsigned long long* traffic, unsigned long long* tround,
                                    uint32_t* bar) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s == 0) {
-    *traffic = 0ull;
-    bar[0] = 0u;  // the grid barrier starts clean (the status word is the caller's)
-    bar[1] = 0u;
-  }
-  if (s < kBatchRoundSlots * 4) tround[s] = 0ull;
+  batch_launch_reset(traffic, tround, bar, s);
   if (s >= count) return;
-  SegDesc& d = segs[s];
-  constexpr uint32_t K = sizeof(T), A = 16 / sizeof(T);
-  const uintptr_t addr = reinterpret_cast<uintptr_t>(d.keys);
-  uint64_t h = ((16 - (addr & 15)) & 15) / K;
-  if (h > d.n) h = d.n;
-  d.h = h;
-  d.be = h + ((d.n - h) / A) * A;
-  d.lo = h;
-  d.hi = d.be;
-  d.level = 0;
-  d.state = kSegOpen;
-  // the offsets X of a segment depend on the batch seed and the segment's
-  // salt only, not on its place in the list
-  d.seed = sm_stream(seed, d.salt);
-  d.vmin = ~0ull;
-  d.vmax = 0ull;
-  d.count = 0ull;
-  d.body_count = 0ull;
-  d.t = 0ull;
+  batch_seg_init<T>(segs[s], seed);
 }
 
 }  // namespace
@@ -627,17 +603,21 @@ BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint
 
 template <typename T>
 cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
-                           const BatchScratch& Bs, const BatchTuning& tune, LaunchCfg& cfg) {
+                           const BatchScratch& Bs, const BatchTuning& tune, LaunchCfg& cfg,
+                           bool records_ready) {
   using R = Tr<T, false>;
   cudaStream_t st = cfg.stream;
   if (count == 0) return cudaSuccess;
-  const uint32_t setup_threads = count > kBatchRoundSlots * 4 ? count : kBatchRoundSlots * 4;
-  batch_setup_kernel<T><<<(setup_threads + 255) / 256, 256, 0, st>>>(d_segs, count, seed,
-                                                                      Bs.totals + 2, Bs.tround,
-                                                                      Bs.bar);
-  cfg.launches++;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (!records_ready) {
+    const uint32_t setup_threads = count > kBatchRoundSlots * 4 ? count : kBatchRoundSlots * 4;
+    batch_setup_kernel<T><<<(setup_threads + 255) / 256, 256, 0, st>>>(d_segs, count, seed,
+                                                                        Bs.totals + 2, Bs.tround,
+                                                                        Bs.bar);
+    cfg.launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   BatchArgs a;
   a.splits = d_splits;
   a.max_rounds = kMaxLevels;
@@ -679,9 +659,9 @@ template cudaError_t batched_prepare<uint32_t>(int, uint32_t*);
 
 template cudaError_t launch_batched<uint64_t>(SegDesc*, uint32_t, uint64_t, uint64_t*,
                                               const BatchScratch&, const BatchTuning&,
-                                              LaunchCfg&);
+                                              LaunchCfg&, bool);
 template cudaError_t launch_batched<uint32_t>(SegDesc*, uint32_t, uint64_t, uint64_t*,
                                               const BatchScratch&, const BatchTuning&,
-                                              LaunchCfg&);
+                                              LaunchCfg&, bool);
 
 }  // namespace lp

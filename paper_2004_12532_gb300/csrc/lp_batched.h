@@ -90,12 +90,16 @@ BatchScratch carve_batch_scratch(void* base, uint32_t count, uint32_t* bar, uint
 template <typename T>
 cudaError_t batched_prepare(int device, uint32_t* grid);
 
-// One persistent launch over the segments.  The grid barrier is reset by the
-// launch; the status word is not (a caller resets it once per call, so a
-// failure of any launch of the call stays visible).
+// One persistent launch over the segments, after a set-up launch that gives
+// every record its engine state and resets the grid barrier and the tallies
+// (lp_batch_init.cuh); with records_ready the caller has done that on the
+// device already (for `seed`) and only the persistent launch runs.  The
+// status word is not reset (a caller resets it once per call, so a failure of
+// any launch of the call stays visible).
 template <typename T>
 cudaError_t launch_batched(SegDesc* d_segs, uint32_t count, uint64_t seed, uint64_t* d_splits,
-                           const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg);
+                           const BatchScratch& B, const BatchTuning& tune, LaunchCfg& cfg,
+                           bool records_ready = false);
 
 // Quicksort on the batched partition (lp_quicksort.cu).  `staging`:
 // quicksort_staging_bytes(n) of pinned host memory for the per-level job

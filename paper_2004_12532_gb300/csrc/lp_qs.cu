@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lp_batch_init.cuh"
 #include "lp_qs.cuh"
 #include "lp_qs_level.cuh"
 #include "lp_qs_sort.cuh"
@@ -21,6 +22,27 @@ __global__ void qs_build_kernel(const QsJob* jobs, SegDesc* segs) {
   if (i >= J.count) return;
   segs[J.seg_base + i] =
       qs_item_record<T>(static_cast<T*>(J.keys), J.items[i], J.seed, J.level, J.samples);
+}
+
+// One level's set-up of one slice in one launch: the job record to the device
+// (the level's later kernels read it there), the level counts reset (first
+// slice), and every item's segment record built with its engine state, in
+// place of the batched engine's own set-up launch.
+template <typename T>
+__global__ void qs_level_start_kernel(const QsJob J, QsJob* d_job, SegDesc* segs,
+                                      uint64_t batch_seed, unsigned long long* traffic,
+                                      unsigned long long* tround, uint32_t* bar,
+                                      uint32_t reset_counts) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *d_job = J;
+    if (reset_counts) *J.lc = QsLevelCounts{0u, 0u, 0u, 0u};
+  }
+  batch_launch_reset(traffic, tround, bar, i);
+  if (i >= J.count) return;
+  SegDesc d = qs_item_record<T>(static_cast<T*>(J.keys), J.items[i], J.seed, J.level, J.samples);
+  batch_seg_init<T>(d, batch_seed);
+  segs[J.seg_base + i] = d;
 }
 
 __global__ void qs_split_kernel(const QsJob* jobs, const SegDesc* segs, const uint64_t* splits,
@@ -79,6 +101,16 @@ cudaError_t launch_qs_build(const QsJob* jobs, uint32_t njobs, uint32_t max_coun
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_qs_level_start(const QsJob& J, QsJob* d_job, SegDesc* segs,
+                                  uint64_t batch_seed, const BatchScratch& B, bool reset_counts,
+                                  cudaStream_t st) {
+  const uint32_t threads = J.count > kBatchRoundSlots * 4 ? J.count : kBatchRoundSlots * 4;
+  qs_level_start_kernel<T><<<(threads + 255) / 256, 256, 0, st>>>(
+      J, d_job, segs, batch_seed, B.totals + 2, B.tround, B.bar, reset_counts ? 1u : 0u);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_qs_split(const QsJob* jobs, uint32_t njobs, uint32_t max_count,
                             const SegDesc* segs, const uint64_t* splits,
                             const unsigned long long* traffic, unsigned long long* traffic_acc,
@@ -130,6 +162,10 @@ template cudaError_t launch_qs_build<uint64_t>(const QsJob*, uint32_t, uint32_t,
                                                cudaStream_t);
 template cudaError_t launch_qs_build<uint32_t>(const QsJob*, uint32_t, uint32_t, SegDesc*,
                                                cudaStream_t);
+template cudaError_t launch_qs_level_start<uint64_t>(const QsJob&, QsJob*, SegDesc*, uint64_t,
+                                                     const BatchScratch&, bool, cudaStream_t);
+template cudaError_t launch_qs_level_start<uint32_t>(const QsJob&, QsJob*, SegDesc*, uint64_t,
+                                                     const BatchScratch&, bool, cudaStream_t);
 template cudaError_t launch_qs_small_sort<uint64_t>(const QsJob*, uint32_t, uint32_t,
                                                     cudaStream_t);
 template cudaError_t launch_qs_small_sort<uint32_t>(const QsJob*, uint32_t, uint32_t,

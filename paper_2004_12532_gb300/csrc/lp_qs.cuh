@@ -69,6 +69,16 @@ template <typename T>
 cudaError_t launch_qs_build(const QsJob* jobs, uint32_t njobs, uint32_t max_count, SegDesc* segs,
                             cudaStream_t st);
 
+// One slice's level set-up in one launch (the one-array quicksort): writes J
+// to d_job, where the level's split and sort kernels read it, resets J.lc when
+// reset_counts (the level's first slice), and builds the slice's segment
+// records as launch_qs_build does, with the batched engine's set-up for
+// `batch_seed` (launch_batched then runs with records_ready).
+template <typename T>
+cudaError_t launch_qs_level_start(const QsJob& J, QsJob* d_job, SegDesc* segs,
+                                  uint64_t batch_seed, const BatchScratch& B, bool reset_counts,
+                                  cudaStream_t st);
+
 // Children of every partitioned item after the batched launch; adds the keys
 // that launch streamed (*traffic) to *traffic_acc.
 cudaError_t launch_qs_split(const QsJob* jobs, uint32_t njobs, uint32_t max_count,

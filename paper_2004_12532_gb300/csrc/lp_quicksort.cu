@@ -139,16 +139,21 @@ cudaError_t launch_quicksort(T* keys, uint64_t n, uint64_t seed, uint32_t sample
       J.samples = samples;
       J.local_cut = 0;
     }
-    if (levels > 0) e = cudaMemsetAsync(L.lc, 0, sizeof(QsLevelCounts), st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(L.jobs, hjobs, nrec * sizeof(QsJob), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = mark(0);
-    if (e != cudaSuccess) return e;
+    // a level with items: each slice's first launch writes its job record,
+    // resets the level counts (first slice) and sets up the records -- one
+    // launch before the persistent one, where a copy, a reset and two
+    // set-up kernels would each wait for the host to issue them
+    if (nslices == 0) {  // the small-only first level: its record for the sort
+      e = cudaMemcpyAsync(L.jobs, hjobs, sizeof(QsJob), cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    if ((e = mark(0)) != cudaSuccess) return e;
     for (uint32_t k = 0; k < nslices; k++) {
       const uint32_t cnt = hjobs[k].count;
-      if ((e = launch_qs_build<T>(L.jobs + k, 1, cnt, L.segs, st)) != cudaSuccess) return e;
+      e = launch_qs_level_start<T>(hjobs[k], L.jobs + k, L.segs, batch_seed, Bs, k == 0, st);
+      if (e != cudaSuccess) return e;
       cfg.launches++;
-      e = launch_batched<T>(L.segs, cnt, batch_seed, L.splits, Bs, tune, cfg);
+      e = launch_batched<T>(L.segs, cnt, batch_seed, L.splits, Bs, tune, cfg, true);
       if (e != cudaSuccess) return e;
       e = launch_qs_split(L.jobs + k, 1, cnt, L.segs, L.splits, Bs.totals + 2, L.acc, st);
       if (e != cudaSuccess) return e;
