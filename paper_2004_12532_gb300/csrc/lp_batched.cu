@@ -168,9 +168,9 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
               d.b = 1;
               in[3] = 1;
             } else if (level > 0 && m <= (uint64_t)a.mc_slices * cta_cap) {
-              // a residual range c > 1 CTAs hold: finished on
-              // chip by c CTAs, a stable partition (the same as one CTA's);
-              // its keys are counted when it runs
+              // a residual range c > 1 CTAs hold: finished on chip by c
+              // CTAs, a stable partition (the same as one CTA's); its keys
+              // are counted when it runs
               const uint64_t c = (m + cta_cap - 1) / cta_cap;
               d.g = 0;
               d.b = c;
@@ -306,8 +306,9 @@ __global__ void __launch_bounds__(Tr<T, false>::Threads) batched_kernel(SegDesc*
       // count and waits until every slice of the finish is staged (all of the
       // range's keys on chip); then it writes its predecessors and successors
       // to their final places, and the last slice of a finish to complete
-      // places the head and tail.  A finish has at most gridDim.x slices and
-      // a CTA holds one slice at a time, taken in order, so the slices a CTA
+      // places the head and tail.  A finish has at most a.mc_slices <=
+      // gridDim.x slices and a CTA holds one slice at a time, taken in order
+      // (all CTAs resident: a cooperative launch), so the slices a CTA
       // waits for are taken by CTAs that wait for nothing else: every wait
       // ends.  The counts live in windows of a.mc_window slices (at least
       // any finish's), grid barriers between; a finish cut by a window's end
